@@ -1,0 +1,89 @@
+"""Seeded synthetic inputs: phantoms, noise and random test vectors.
+
+This module holds none of the method's arithmetic (no projection, no BSGD
+step); it only draws inputs, so that the tests can feed the same data to the
+CUDA library and to the FP64 oracle. It imports nothing from either.
+
+The paper's data (a Shepp-Logan phantom, the TIGRE skull) are replaced by
+random ellipses / ellipsoids of the same kind:
+  * 2D: n ellipses, drawn in the order cx, cy ~ U[-.6, .6]; a, b ~ U[.05, .4];
+    phi ~ U[0, pi); rho ~ U[0, 1]; densities add up; sampled at pixel centres
+    in normalised coordinates [-1, 1];
+  * 3D: centres ~ U[-.6, .6]^3, semi-axes ~ U[.05, .4]^3, rotation about z by
+    phi ~ U[0, pi), rho ~ U[0, 1].
+"""
+import math
+
+import numpy as np
+
+
+def _norm_coords(n: int) -> np.ndarray:
+    return (np.arange(n, dtype=np.float64) + 0.5) * (2.0 / n) - 1.0
+
+
+def ellipse_phantom(nx: int, ny: int, n_ellipses: int = 6, seed: int = 0) -> np.ndarray:
+    """[ny, nx] float64 image of random ellipses."""
+    rng = np.random.default_rng(seed)
+    X, Y = np.meshgrid(_norm_coords(nx), _norm_coords(ny), indexing="xy")
+    img = np.zeros((ny, nx))
+    for _ in range(n_ellipses):
+        cx, cy = rng.uniform(-0.6, 0.6, size=2)
+        a, b = rng.uniform(0.05, 0.4, size=2)
+        phi = rng.uniform(0.0, math.pi)
+        rho = rng.uniform(0.0, 1.0)
+        c, s = math.cos(phi), math.sin(phi)
+        xr = c * (X - cx) + s * (Y - cy)
+        yr = -s * (X - cx) + c * (Y - cy)
+        img[(xr / a) ** 2 + (yr / b) ** 2 <= 1.0] += rho
+    return img
+
+
+def ellipsoid_phantom(nx: int, ny: int, nz: int, n_ellipsoids: int = 10, seed: int = 0) -> np.ndarray:
+    """[nz, ny, nx] float32 volume of random ellipsoids (built slice by slice to
+    keep memory at one slice of float64)."""
+    rng = np.random.default_rng(seed)
+    params = []
+    for _ in range(n_ellipsoids):
+        ctr = rng.uniform(-0.6, 0.6, size=3)
+        ax = rng.uniform(0.05, 0.4, size=3)
+        phi = rng.uniform(0.0, math.pi)
+        rho = rng.uniform(0.0, 1.0)
+        params.append((ctr, ax, math.cos(phi), math.sin(phi), rho))
+    X, Y = np.meshgrid(_norm_coords(nx), _norm_coords(ny), indexing="xy")
+    zc = _norm_coords(nz)
+    vol = np.zeros((nz, ny, nx), dtype=np.float32)
+    for k in range(nz):
+        sl = np.zeros((ny, nx))
+        for ctr, ax, c, s, rho in params:
+            dz = (zc[k] - ctr[2]) / ax[2]
+            if dz * dz > 1.0:
+                continue
+            xr = c * (X - ctr[0]) + s * (Y - ctr[1])
+            yr = -s * (X - ctr[0]) + c * (Y - ctr[1])
+            sl[(xr / ax[0]) ** 2 + (yr / ax[1]) ** 2 + dz * dz <= 1.0] += rho
+        vol[k] = sl
+    return vol
+
+
+def poisson_log_data(line_integrals: np.ndarray, i0: float, seed: int) -> np.ndarray:
+    """Transmission data with Poisson counts: N ~ Poisson(I0 exp(-p)),
+    y = -ln(max(N, 1) / I0). Returned as float32."""
+    rng = np.random.default_rng(seed)
+    counts = rng.poisson(i0 * np.exp(-np.asarray(line_integrals, dtype=np.float64)))
+    return (-np.log(np.maximum(counts, 1) / i0)).astype(np.float32)
+
+
+def gaussian_noise_at_snr(y: np.ndarray, snr_db: float, seed: int) -> np.ndarray:
+    """y + e with white Gaussian e scaled so that 20 log10(||y|| / ||e||) = snr_db."""
+    rng = np.random.default_rng(seed)
+    e = rng.standard_normal(y.shape)
+    e *= np.linalg.norm(y) / (np.linalg.norm(e) * 10.0 ** (snr_db / 20.0))
+    return y + e
+
+
+def uniform_array(shape, seed: int, lo: float = 0.0, hi: float = 1.0, dtype=np.float64) -> np.ndarray:
+    return np.random.default_rng(seed).uniform(lo, hi, size=shape).astype(dtype)
+
+
+def normal_array(shape, seed: int, dtype=np.float64) -> np.ndarray:
+    return np.random.default_rng(seed).standard_normal(size=shape).astype(dtype)
