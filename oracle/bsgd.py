@@ -247,7 +247,9 @@ class BSGDState:
             self.x[vox] += prm.mu * self.g[vox]
         self.it += 1
         if prm.tv_lambda > 0.0 and self.it % prm.epoch_len == 0:   # Algorithm 4
-            self.x = tv_prox(self.x.reshape(geom.vol_shape), prm.mu * prm.tv_lambda,
+            # Eq. 10 is the TV of a 2D image; volumes use the 3D extension
+            shape = geom.vol_shape if geom.nz > 1 else (geom.ny, geom.nx)
+            self.x = tv_prox(self.x.reshape(shape), prm.mu * prm.tv_lambda,
                              prm.tv_iters).reshape(-1)
         self.history.append(sel)
         return sel
