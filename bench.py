@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Benchmark of the BSGD hot path on one GB300 (or N replicas).
+
+Workload (the 3D cone-beam configuration): 256^3 voxels of 1 mm, 360 views over
+360 deg, 256 x 256 detector of 1.6 mm pixels, source-origin 500 mm,
+source-detector 1000 mm; seeded 10-ellipsoid phantom (attenuation 0.01/mm x
+density), Poisson data with I0 = 1e4; BSGD with 8 angular row blocks x 8 z-slab
+column blocks, alpha = gamma = 1/8, pair sampling weighted by the residual mass
+on each pair's detector band, step rho / max_J ||A^J||^2 (rho = 0.25, FP64 power
+iteration). One step = one epoch = 64 block iterations (device sampling, FP with
+the fused residual update, BP of the residual change, block update).
+
+Metric: voxel-ray updates per second (FP + BP), one update being a (ray, voxel)
+pair of positive length, counted exactly per pair by the library's count pass.
+
+  python bench.py [--gpus N --steps K --warmup W]          # CUDA library
+  python bench.py --impl reference [--steps K --warmup W]  # FP64 CPU oracle
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GEOM = dict(kind="cone3d", nx=256, ny=256, nz=256, dx=1.0, dy=1.0, dz=1.0, n_views=360,
+            nu=256, nv=256, du=1.6, dv=1.6, dso=500.0, dsd=1000.0)
+M, N = 8, 8
+ITERS_PER_EPOCH = 64
+KAPPA = 0.01          # attenuation per mm of unit density
+I0 = 1e4
+RHO = 0.25
+WORKLOAD = ("cone3d 256^3 (1 mm), 360 views / 360 deg, 256x256 det (1.6 mm), DSO 500 / DSD 1000, "
+            "10 ellipsoids, Poisson I0=1e4; BSGD 8x8 blocks, alpha=gamma=1/8, residual-weighted "
+            "pairs; step = 1 epoch = 64 block iterations")
+METRIC = "GVox-ray updates/s (FP+BP)"
+UNIT = "GVox-ray/s"
+# FP32-pipe instructions every Siddon update needs at the least: two minima for
+# the next crossing, the segment difference, the accumulate / weight product and
+# the recomputed crossing.
+ALU_OPS_PER_UPDATE = 5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, flag in zip(names, parts[4:8]):
+                if flag.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# inputs
+
+def make_inputs(B, gg, torch, dev, seed_offset=0):
+    """Phantom -> line integrals with the library's own FP -> Poisson data."""
+    import numpy as np
+    from paper_1903_11874_gb300 import synth
+    vol = synth.ellipsoid_phantom(256, 256, 256, 10, seed=0 + seed_offset) * KAPPA
+    xt = torch.from_numpy(vol.reshape(-1)).to(dev)
+    p = torch.zeros(gg.n_rows, device=dev)
+    B.bsgd_forward_project(gg, xt, p)
+    y = synth.poisson_log_data(p.cpu().numpy(), I0, seed=2 + seed_offset)
+    return np.ascontiguousarray(y), xt
+
+
+def algorithmic_bytes(gg, n_pairs_avg_rays, storage_bytes=4):
+    """Compulsory DRAM bytes of one FP and one BP launch (one pair), per the
+    kernels' data flow: FP reads x_J and, per traced ray, y, every z^j and r, and
+    writes z^J and r; BP reads r and r~^J, writes r~^J and read-modify-writes g_J."""
+    vox_j = gg.n_cols // N
+    rays = n_pairs_avg_rays
+    fp = vox_j * storage_bytes + rays * storage_bytes * (1 + N + 1 + 2)
+    bp = rays * storage_bytes * 3 + vox_j * 8
+    return fp, bp
+
+
+def run_cuda(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1903_11874_gb300 import binding as B
+
+    rank, local, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    B.load()
+    gg = B.Geometry(M=M, N=N, **GEOM)
+    y_np, _ = make_inputs(B, gg, torch, dev, seed_offset=rank)
+    y = torch.from_numpy(y_np).to(dev)
+    prm = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_STRIP, rho=RHO,
+                        power_iters=30, pair_sampling=B.PAIRS_RESIDUAL, seed=1 + rank)
+    st = B.State(gg, prm, y)
+    mu = st.query()["mu"]
+    x = torch.zeros(gg.n_cols, device=dev)
+    for _ in range(args.warmup):
+        st.block_step(x, ITERS_PER_EPOCH)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    q0 = st.query()
+    st.profile(True)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st.block_step(x, ITERS_PER_EPOCH)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = st.read_profile()
+    q1 = st.query()
+    updates = q1["updates"] - q0["updates"]
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        u = torch.tensor([float(updates)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        ms, updates_all = float(t.item()), float(u.item())
+    else:
+        updates_all = float(updates)
+    value = updates_all / (ms * 1e-3) / 1e9
+
+    # ---- roofline of the dominant kernel (FP or BP), timed live above
+    peaks = measured_peaks()
+    iters = args.steps * ITERS_PER_EPOCH
+    upd_per_launch = updates / 2.0 / iters            # FP and BP each do half
+    dom = max(("fp", "bp"), key=lambda k: prof[k]["ms"])
+    launch_ms = prof[dom]["ms"] / max(prof[dom]["launches"], 1)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = 152 * 128 * sm_max * 1e6 / 1e12         # FP32-pipe instr/s, in T/s
+    achieved = ALU_OPS_PER_UPDATE * upd_per_launch / (launch_ms * 1e-3) / 1e12
+    avg_rays = np.mean([gg.pair_rays(i, j) for i in range(M) for j in range(N)])
+    fpb, bpb = algorithmic_bytes(gg, avg_rays)
+    dom_bytes = fpb if dom == "fp" else bpb
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_ach = dom_bytes / (launch_ms * 1e-3) / 1e9
+    roofline = {
+        "bound": "alu", "kernel": "%s_solve_kernel" % dom,
+        "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
+        "unit": "T FP32-pipe instr/s (%d per update)" % ALU_OPS_PER_UPDATE,
+        "frac": round(achieved / alu_peak, 4), "traffic": None,
+        "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % sm_max,
+        "launch_ms": round(launch_ms, 4), "updates_per_launch": int(upd_per_launch),
+        "hbm_algorithmic_gbs": round(hbm_ach, 1), "hbm_peak_gbs": hbm_peak,
+        "hbm_frac": round(hbm_ach / hbm_peak, 4),
+    }
+    stages = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items()
+              if v["launches"]}
+    launches = sum(v["launches"] for v in prof.values())
+
+    # ---- end to end through the public one-call API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        yh = torch.from_numpy(y_np).pin_memory()
+        xh = torch.zeros(gg.n_cols, dtype=torch.float32).pin_memory()
+        pe = B.SolveParams(alpha=1 / M, gamma=1 / N, epochs=1, step_rule=B.STEP_FIXED, mu=mu,
+                           pair_sampling=B.PAIRS_RESIDUAL, seed=1 + rank)
+        B.bsgd_solve(gg, pe, yh, xh)       # warm-up
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        upd_e2e = 0
+        for _ in range(args.steps):
+            rep = B.bsgd_solve(gg, pe, yh, xh)
+            upd_e2e += rep["updates"]
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            u = torch.tensor([float(upd_e2e)], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dist.all_reduce(u, op=dist.ReduceOp.SUM)
+            t_e2e, upd_e2e = float(t.item()), float(u.item())
+        e2e = {"value": round(upd_e2e / t_e2e / 1e9, 3), "unit": UNIT,
+               "h2d_bytes_per_step": int(gg.n_rows * 4), "d2h_bytes_per_step": int(gg.n_cols * 4),
+               "api": "bsgd_solve (1 epoch per call, pinned host y and x, fixed mu)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(y_np, mu, n_iters=2)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ellipsoid phantom, Poisson noise)",
+            "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (state 1.9 GB; one iteration touches ~150 MB)",
+                       "mu": mu, "residual_norm_end": q1["residual_norm"]},
+            "gpu_launches": int(launches), "stages_ms": stages,
+            "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the FP64 oracle as it stands, on a bounded sample of the workload
+
+def oracle_sample(y_np, mu, n_iters):
+    """n_iters BSGD iterations of the oracle (snapshot form, residual-weighted
+    pairs) on the same workload; returns (updates, seconds, threads)."""
+    import numpy as np
+    from oracle import bsgd as OB
+    from oracle import projector as OP
+    og = OP.Geometry(**GEOM)
+    prm = OB.Params(M, N, 1 / M, 1 / N, mu, seed=1, pair_sampling="residual")
+    st = OB.BSGDState(og, np.asarray(y_np, dtype=np.float64), prm)
+    t0 = time.perf_counter()
+    for _ in range(n_iters):
+        st.step()
+    dt = time.perf_counter() - t0
+    upd = 0
+    for sel in st.history:
+        for (i, j) in sel.pairs:
+            rows = OP.rows_of_views(og, OP.row_block_views(og, M, i))
+            upd += 2 * OP.count_rows(og, rows, OP.column_block(og, N, j))
+    return upd, dt, OP.num_threads()
+
+
+def cpu_baseline(y_np, mu, n_iters):
+    upd, dt, threads = oracle_sample(y_np, mu, n_iters)
+    return {"value": round(upd / dt / 1e9, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d BSGD iterations (one (row block, z-slab) pair each) of the workload, "
+                      "FP64 oracle, %.1f s" % (n_iters, dt)}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_1903_11874_gb300 import synth
+    from oracle import projector as OP
+    og = OP.Geometry(**GEOM)
+    vol = synth.ellipsoid_phantom(256, 256, 256, 10, seed=0).astype(np.float64) * KAPPA
+    p = OP.fp(og, vol.reshape(-1)).reshape(-1)
+    y = synth.poisson_log_data(p, I0, seed=2)
+    from oracle import bsgd as OB
+    mu = RHO / 1.0e5          # a fixed step of the right scale; the timing does not depend on it
+    prm = OB.Params(M, N, 1 / M, 1 / N, mu, seed=1, pair_sampling="residual")
+    st = OB.BSGDState(og, y.astype(np.float64), prm)
+    for _ in range(args.warmup):
+        st.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st.step()
+    dt = time.perf_counter() - t0
+    upd = 0
+    for sel in st.history[args.warmup:]:
+        for (i, j) in sel.pairs:
+            rows = OP.rows_of_views(og, OP.row_block_views(og, M, i))
+            upd += 2 * OP.count_rows(og, rows, OP.column_block(og, N, j))
+    value = upd / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt * 1e3 / args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded ellipsoid phantom, Poisson noise)",
+        "config": {"workload": WORKLOAD, "step": "1 BSGD block iteration per step (bounded sample)"},
+        "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": OP.num_threads(),
+                         "kind": "oracle",
+                         "sample": "%d oracle BSGD iterations after %d warm-up" % (args.steps, args.warmup)},
+        "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

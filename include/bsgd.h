@@ -1,0 +1,322 @@
+/*
+ * bsgd.h -- C ABI of the GB300 (sm_103a) BSGD hot path.
+ *
+ * Block stochastic gradient descent for tomographic reconstruction
+ * (Gao, Biguri and Blumensath, arXiv:1903.11874): the on-the-fly Siddon
+ * forward projection of a sampled row block, the matched back projection into a
+ * sampled column block, the aggregated block gradient step, device-side block
+ * sampling (uniform, sub-detector importance sampling, residual-weighted) and
+ * the TV proximal step of BSGD-TV.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every call returns a bsgd_status; nothing throws across the ABI. After a
+ *    failure bsgd_last_error() returns a message for the calling thread.
+ *  - Pointers named "device" must be CUDA device (or managed) memory owned by
+ *    the caller; the library never frees them. bsgd_solve() alone also accepts
+ *    host pointers and copies them itself.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
+ *    asynchronous on that stream unless their comment says they synchronise.
+ *  - Volumes are stored [z][y][x] (x fastest), sinograms [view][v][u]
+ *    (u fastest). Element types are given by bsgd_dtype.
+ *  - The library owns the geometry tables and the solver state behind the
+ *    opaque handles below; each has an explicit destroy call.
+ *
+ * Model (Sec. 1, Eqs. 1-2): y = A x + e, min_x 1/2 ||y - A x||^2, where A_ij >= 0
+ * is the length of ray i inside voxel j (Siddon). A is never stored; every FP and
+ * BP traces the rays on the fly. Rows are split into M row blocks I_i (whole
+ * views), columns into N column blocks J_j (slabs of z planes for volumes, of y
+ * rows for 2D images), Sec. 2, Eq. 3.
+ */
+#ifndef BSGD_H
+#define BSGD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BSGD_OK = 0,
+    BSGD_ERR_INVALID_ARG = 1, /* bad size, pointer, enum or combination       */
+    BSGD_ERR_OOM = 2,         /* device or host allocation failed             */
+    BSGD_ERR_CUDA = 3,        /* a CUDA call failed (message has the reason)  */
+    BSGD_ERR_TIMEOUT = 4,     /* a bounded wait ran out                       */
+    BSGD_ERR_BUDGET = 5,      /* request does not fit the memory budget       */
+    BSGD_ERR_STATE = 6        /* call not valid in the object's current state */
+} bsgd_status;
+
+typedef enum { BSGD_F32 = 0, BSGD_BF16 = 1, BSGD_F16 = 2 } bsgd_dtype;
+
+typedef enum {
+    BSGD_PAR2D = 0,  /* parallel beam, one image slice (nz = nv = 1)          */
+    BSGD_FAN2D = 1,  /* fan beam, one image slice (nz = nv = 1)               */
+    BSGD_CONE3D = 2  /* circular cone beam                                    */
+} bsgd_geom_kind;
+
+/*
+ * Scan geometry (the paper fixes none of these conventions; they are the ones
+ * the library and its tests share):
+ *  - voxel i along an axis with n voxels of size h spans
+ *    [-n h / 2 + i h, -n h / 2 + (i + 1) h]; the rotation centre is the origin;
+ *  - detector pixel k has centre (k - (n - 1) / 2) * size;
+ *  - PAR2D view angle t: rays along (cos t, sin t, 0), detector axis
+ *    (-sin t, cos t, 0);
+ *  - FAN2D / CONE3D view angle b: source dso (cos b, sin b, 0), detector centre
+ *    -(dsd - dso)(cos b, sin b, 0), axes u = (-sin b, cos b, 0), v = (0, 0, 1);
+ *    one ray from the source to each pixel centre;
+ *  - angles == NULL means a * pi / n_views (PAR2D) or a * 2 pi / n_views;
+ *  - a ray lying exactly in a voxel face belongs to the voxel on the + side.
+ */
+typedef struct {
+    int kind;                   /* bsgd_geom_kind                                  */
+    int nx, ny, nz;             /* voxels                                          */
+    double dx, dy, dz;          /* voxel size (mm)                                 */
+    int n_views;
+    const double *angles;       /* host, n_views radians, or NULL (uniform)        */
+    int nu, nv;                 /* detector pixels                                 */
+    double du, dv;              /* detector pixel size (mm)                        */
+    double dso, dsd;            /* source-origin, source-detector distance (mm)   */
+    const int32_t *view_block;  /* host, n_views row-block ids in [0, M), or NULL
+                                   for the interleaved partition I_i = {a : a mod M = i} */
+} bsgd_geometry_desc;
+
+typedef struct bsgd_geometry bsgd_geometry;
+typedef struct bsgd_state bsgd_state;
+
+typedef struct {
+    int64_t n_rows;             /* r = n_views * nv * nu                           */
+    int64_t n_cols;             /* c = nx * ny * nz                                */
+    int M, N;
+    int block_axis;             /* 1 (y strips, 2D) or 2 (z slabs, 3D)             */
+    int max_views_per_block;
+    int64_t max_block_cols;     /* voxels in the largest column block              */
+} bsgd_geometry_info;
+
+const char *bsgd_last_error(void);
+const char *bsgd_status_string(bsgd_status s);
+
+/*
+ * Build the ray and block tables of a geometry and upload them to the current
+ * CUDA device (Sec. 2, Eq. 3: M row blocks of whole views, N column blocks).
+ * Synchronous. *out receives a handle owned by the caller.
+ * Errors: INVALID_ARG (sizes <= 0, nz/nv != 1 for 2D kinds, dsd <= dso or a
+ * volume that reaches the source for divergent beams, M > n_views, N > planes
+ * along the block axis, view_block ids out of range or a block without views),
+ * OOM, CUDA.
+ */
+bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int M, int N,
+                                 bsgd_geometry **out);
+bsgd_status bsgd_geometry_destroy(bsgd_geometry *g);
+bsgd_status bsgd_geometry_get_info(const bsgd_geometry *g, bsgd_geometry_info *out);
+
+/*
+ * Rays the projector traces for the pair (row block i, column block j): the
+ * detector band of J_j's shadow (with a one-pixel margin) summed over the views
+ * of I_i. Rays outside the band cannot meet J_j (Sec. 2.1: a block projects
+ * onto part of the detector only). Host-side; *out is a host int64.
+ */
+bsgd_status bsgd_geometry_pair_rays(const bsgd_geometry *g, int i, int j, int64_t *out);
+
+/*
+ * Forward projection y_S (= or +=) A_S^B x_B  (Sec. 1 after Eq. 2; the summand
+ * A_I^J x_J of Sec. 2 and Algorithm 1's FP step).
+ *  x: device, batch * n_cols elements of type xt (whole volumes; only the
+ *     voxels of the selected column blocks are read).
+ *  y: device, batch * n_rows elements of type yt. Rows of the selected row
+ *     blocks are written (accumulate = 0) or added to (accumulate = 1); other
+ *     rows are untouched.
+ *  row_blocks / col_blocks: host arrays of block ids (n_rb / n_cb entries), or
+ *     NULL to select every block. Ids must be distinct and in range.
+ * Deterministic: each ray sums its segments in traversal order.
+ * Errors: INVALID_ARG, CUDA (launch failure).
+ */
+bsgd_status bsgd_forward_project(const bsgd_geometry *g, const void *x, bsgd_dtype xt,
+                                 void *y, bsgd_dtype yt,
+                                 const int32_t *row_blocks, int n_rb,
+                                 const int32_t *col_blocks, int n_cb,
+                                 int accumulate, int batch, void *stream);
+
+/*
+ * Back projection x_B (= or +=) scale * (A_S^B)^T r_S, the exact transpose of
+ * bsgd_forward_project (Algorithm 1's BP step).
+ *  r: device, batch * n_rows elements of type rt; rows outside the selected
+ *     row blocks are not read.
+ *  x: device, batch * n_cols float32 (BSGD_F32 only: the scatter accumulates
+ *     with float atomics). With accumulate = 0 the voxels of the selected
+ *     column blocks are cleared first; other voxels are untouched.
+ * Not bit-reproducible run to run (atomic order); results agree to float
+ * rounding.
+ */
+bsgd_status bsgd_back_project(const bsgd_geometry *g, const void *r, bsgd_dtype rt,
+                              void *x, bsgd_dtype xt,
+                              const int32_t *row_blocks, int n_rb,
+                              const int32_t *col_blocks, int n_cb,
+                              float scale, int accumulate, int batch, void *stream);
+
+/*
+ * Number of voxel-ray updates of one FP (or one BP) over the selected blocks:
+ * the (ray, voxel) pairs whose segment is longer than 1e-4 of the smallest
+ * voxel edge (shorter pieces occur only where a ray passes, up to rounding,
+ * through a voxel edge or corner, and vanish in exact arithmetic).
+ * Synchronous; *out is a host int64.
+ */
+bsgd_status bsgd_count_updates(const bsgd_geometry *g,
+                               const int32_t *row_blocks, int n_rb,
+                               const int32_t *col_blocks, int n_cb,
+                               int64_t *out, void *stream);
+
+/*
+ * Step-size estimate lambda_J ~ ||A^J||_2^2 of column block j by power
+ * iteration: v0 = 1 / sqrt|J| on J, v <- A^T A v / ||A^T A v|| (iters times),
+ * lambda = ||A^J v||^2. Vector state, norms and lambda are FP64 on the device;
+ * the projections read an FP32 copy of v. Synchronous; *lambda_out is host.
+ * rows: every view (row_blocks == NULL) or the listed row blocks.
+ */
+bsgd_status bsgd_power_iteration(const bsgd_geometry *g, int col_block, int iters,
+                                 const int32_t *row_blocks, int n_rb,
+                                 double *lambda_out, void *stream);
+
+/*
+ * TV proximal step of BSGD-TV (Algorithm 4, Eqs. 9-10):
+ *   x <- argmin_t ||t - x||^2 + 2 kappa TV(t),   kappa = mu * lambda,
+ * isotropic TV from backward differences (a missing neighbour gives 0), solved
+ * by `iters` FGP iterations (Beck and Teboulle 2009) in FP32.
+ *  x: device, n_cols elements of type xt, updated in place.
+ * The library allocates (and frees before returning) the dual field
+ * (ndim * n_cols floats).
+ */
+bsgd_status bsgd_tv_prox(const bsgd_geometry *g, void *x, bsgd_dtype xt,
+                         double kappa, int iters, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Solver                                                                   */
+
+typedef enum {
+    BSGD_STEP_STRIP = 0, /* mu = rho / max_J ||A^J||^2 (power iteration)          */
+    BSGD_STEP_BLOCK = 1, /* mu = rho / max_{i,J} ||A_{I_i}^J||^2                  */
+    BSGD_STEP_FIXED = 2  /* mu given                                              */
+} bsgd_step_rule;
+
+typedef enum {
+    BSGD_PAIRS_UNIFORM = 0,  /* alpha*M row and gamma*N column blocks, uniform   */
+    BSGD_PAIRS_RESIDUAL = 1  /* one pair, p(i,j) ~ residual mass on J's band     */
+} bsgd_pair_sampling;
+
+typedef enum {
+    BSGD_CELLS_NONE = 0,      /* whole views (Algorithm 1)                          */
+    BSGD_CELLS_GEOMETRIC = 1, /* one sub-detector per view, p ~ footprint (Alg. 2) */
+    BSGD_CELLS_UNIFORM = 2    /* one sub-detector per view, uniform (BSGD-RAN)     */
+} bsgd_cell_sampling;
+
+typedef struct {
+    double alpha, gamma;     /* fractions of row / column blocks per iteration      */
+    int epochs;              /* bsgd_solve: epochs of 1/(alpha*gamma) iterations    */
+    int step_rule;           /* bsgd_step_rule                                      */
+    double mu;               /* BSGD_STEP_FIXED: the step                            */
+    double rho;              /* STRIP / BLOCK: fraction of the Lipschitz step        */
+    int power_iters;         /* STRIP / BLOCK power iterations                      */
+    int pair_sampling;       /* bsgd_pair_sampling                                  */
+    int cells;               /* bsgd_cell_sampling                                  */
+    int n_cells;             /* 2 (2D: detector halves) or 4 (3D: quadrants)        */
+    double tv_lambda;        /* > 0: BSGD-TV prox every epoch (Algorithm 4)          */
+    int tv_iters;            /* FGP iterations of the prox                          */
+    int storage;             /* bsgd_dtype of y, x, z^j, r and snapshots             */
+    uint64_t seed;           /* sampling stream (SplitMix64 counter spec)            */
+} bsgd_solve_params;
+
+typedef struct {
+    double residual_norm;    /* ||y - sum_j z^j||_2 in FP64 (the paper's GAP)        */
+    double mu;               /* step in the 1/2 ||.||^2 convention                   */
+    int64_t iteration;       /* iterations done                                      */
+    double epoch;            /* iteration * alpha * gamma                            */
+    int64_t updates;         /* voxel-ray updates done (FP + BP)                     */
+} bsgd_report;
+
+/*
+ * Create solver state for y (device, n_rows elements of type yt, copied into
+ * the state's storage type). The state holds z^j and the residual snapshots
+ * (N * n_rows each), r, the aggregated gradient g (FP32), FP64 residual-norm
+ * tables and the sampler's work list, all in library-owned device memory.
+ * Initial state is Algorithm 1's: g = 0, z = 0, r = y; x starts at 0 (the caller
+ * passes x, zeroed, to bsgd_block_step). Computes mu by power iteration for the
+ * STRIP / BLOCK rules. Synchronous.
+ * Errors: INVALID_ARG (alpha, gamma outside (0, 1], residual pair sampling with
+ * more than one pair per iteration, n_cells not 2 (2D) or 4 (3D) with cells),
+ * OOM, CUDA.
+ */
+bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solve_params *p,
+                              const void *y, bsgd_dtype yt, void *stream,
+                              bsgd_state **out);
+bsgd_status bsgd_state_destroy(bsgd_state *s);
+
+/*
+ * n_iters iterations of BSGD (Algorithm 1; Algorithm 2 with cells; Algorithm 4
+ * when tv_lambda > 0): device-side sampling, FP with fused residual update, BP
+ * of the residual change into g_J, x_J += mu g_J.
+ *  x: device, n_cols elements of the state's storage type, updated in place.
+ *     With BF16 / FP16 storage the state also keeps the low-order part of x
+ *     (compensated storage, so that steps below half an ulp of x accumulate);
+ *     change x only through this call while the state lives.
+ * Asynchronous; no host synchronisation inside.
+ */
+bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void *stream);
+
+/* Progress of the state. Synchronises `stream`. */
+bsgd_status bsgd_state_query(bsgd_state *s, bsgd_report *out, void *stream);
+
+/*
+ * Sampling trace. Each iteration occupies bsgd_trace_stride() int32 entries:
+ * [n_pairs, i_0, j_0, ..., i_{P-1}, j_{P-1}, then per pair the cell chosen for
+ * each view of its row block (-1 when unused)], padded with -1.
+ * bsgd_state_read_trace copies the trace of iterations [0, n) (n <= iterations
+ * done, n * stride <= cap) to host memory; synchronises `stream`.
+ * bsgd_state_set_replay uploads n_iters recorded iterations; the next n_iters
+ * iterations consume them instead of sampling. Synchronous.
+ */
+int64_t bsgd_trace_stride(const bsgd_state *s);
+bsgd_status bsgd_state_read_trace(bsgd_state *s, int32_t *host, int64_t cap,
+                                  int64_t n_iters, void *stream);
+bsgd_status bsgd_state_set_replay(bsgd_state *s, const int32_t *host, int64_t n_iters);
+
+/*
+ * Per-stage device timing of bsgd_block_step (tracing). While enabled, every
+ * iteration records a CUDA event pair on the launching stream around each of
+ * its stages; bsgd_state_read_profile synchronises `stream` and returns, per
+ * stage, the number of kernel launches and their summed device time.
+ * Enabling resets the counters.
+ */
+typedef enum {
+    BSGD_STAGE_SAMPLE = 0,   /* block / cell sampling                         */
+    BSGD_STAGE_FP = 1,       /* forward projection + fused residual update    */
+    BSGD_STAGE_RESIDUAL = 2, /* residual recomputation (several J per row)    */
+    BSGD_STAGE_BP = 3,       /* back projection of the residual change        */
+    BSGD_STAGE_UPDATE = 4,   /* x_J += mu g_J                                 */
+    BSGD_STAGE_TV = 5,       /* TV proximal step (BSGD-TV)                    */
+    BSGD_N_STAGES = 6
+} bsgd_stage;
+
+typedef struct {
+    int64_t launches[BSGD_N_STAGES];
+    double ms[BSGD_N_STAGES];
+} bsgd_profile;
+
+bsgd_status bsgd_state_profile(bsgd_state *s, int enable);
+bsgd_status bsgd_state_read_profile(bsgd_state *s, bsgd_profile *out, void *stream);
+
+/*
+ * One-call reconstruction: state_create, epochs * 1/(alpha*gamma) iterations,
+ * query, destroy. y and x may be host or device pointers (host buffers are
+ * copied in and out inside the call). x holds x0 = 0 on entry and the
+ * reconstruction on return. Synchronous.
+ */
+bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_params *p,
+                       const void *y, bsgd_dtype yt, void *x, bsgd_dtype xt,
+                       bsgd_report *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSGD_H */

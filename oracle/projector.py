@@ -227,8 +227,9 @@ def bp_rows(geom: Geometry, r_rows, rows, block=None, out=None) -> np.ndarray:
 
 
 def count_rows(geom: Geometry, rows, block=None) -> int:
-    """Number of (ray, voxel) pairs of positive length: the voxel-ray updates
-    of one forward (or one back) projection over these rows and block."""
+    """Voxel-ray updates of one forward (or one back) projection over these
+    rows and block: (ray, voxel) pairs longer than 1e-4 of the smallest voxel
+    edge (shorter pieces are edge / corner crossings, zero in exact arithmetic)."""
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     axis, c0, c1 = _block_args(geom, block)
     n = _lib().orc_count_rows(ctypes.byref(geom._c), _iptr(rows), rows.size, axis, c0, c1)

@@ -265,10 +265,16 @@ int orc_bp_rows(const orc_geom *g, const double *r, const int64_t *rows, int64_t
     return err ? -2 : 0;
 }
 
-/* Number of (ray, voxel) pairs with positive length for the rows and block J. */
+/*
+ * Number of (ray, voxel) pairs for the rows and block J whose length exceeds
+ * 1e-4 of the smallest voxel edge. Shorter pieces appear only where a ray
+ * passes (up to rounding) through a voxel edge or corner, and have zero length
+ * in exact arithmetic.
+ */
 int64_t orc_count_rows(const orc_geom *g, const int64_t *rows, int64_t n_rows, int axis, int c0, int c1)
 {
     const int cap = orc_max_crossings(g);
+    const double hmin = fmin(g->dx, fmin(g->dy, g->dz)), eps = 1e-4 * hmin;
     int64_t total = 0;
     int err = 0;
 #pragma omp parallel reduction(+ : total)
@@ -289,7 +295,7 @@ int64_t orc_count_rows(const orc_geom *g, const int64_t *rows, int64_t n_rows, i
                 int cnt = orc_trace(g, p0, p1, vox, len, alpha);
                 for (int t = 0; t < cnt; ++t) {
                     int64_t b = orc_block_coord(g, axis, vox[t]);
-                    if (b >= c0 && b < c1) total += 1;
+                    if (b >= c0 && b < c1 && len[t] > eps) total += 1;
                 }
             }
         }

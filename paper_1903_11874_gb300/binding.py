@@ -1,0 +1,421 @@
+"""Thin ctypes binding of the BSGD C ABI (include/bsgd.h).
+
+Argument marshalling only: every function forwards to the entry point of the
+same name in libbsgd.so, which runs the work in the library's CUDA kernels.
+torch supplies device memory and the current stream. There is no fallback:
+if the library cannot be loaded, every call raises.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+F32, BF16, F16 = 0, 1, 2
+PAR2D, FAN2D, CONE3D = 0, 1, 2
+KINDS = {"par2d": PAR2D, "fan2d": FAN2D, "cone3d": CONE3D}
+STEP_STRIP, STEP_BLOCK, STEP_FIXED = 0, 1, 2
+PAIRS_UNIFORM, PAIRS_RESIDUAL = 0, 1
+CELLS_NONE, CELLS_GEOMETRIC, CELLS_UNIFORM = 0, 1, 2
+
+# Every symbol include/bsgd.h declares.
+EXPORTS = (
+    "bsgd_last_error", "bsgd_status_string", "bsgd_geometry_create", "bsgd_geometry_destroy",
+    "bsgd_geometry_get_info", "bsgd_geometry_pair_rays", "bsgd_forward_project", "bsgd_back_project", "bsgd_count_updates",
+    "bsgd_power_iteration", "bsgd_tv_prox", "bsgd_state_create", "bsgd_state_destroy",
+    "bsgd_block_step", "bsgd_state_query", "bsgd_trace_stride", "bsgd_state_read_trace",
+    "bsgd_state_set_replay", "bsgd_state_profile", "bsgd_state_read_profile", "bsgd_solve",
+)
+STAGES = ("sample", "fp", "residual", "bp", "update", "tv")
+
+
+class BSGDError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), message))
+        self.status = status
+
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "timeout",
+           5: "over budget", 6: "invalid state"}
+
+
+class GeometryDesc(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+        ("n_views", ctypes.c_int),
+        ("angles", ctypes.POINTER(ctypes.c_double)),
+        ("nu", ctypes.c_int), ("nv", ctypes.c_int),
+        ("du", ctypes.c_double), ("dv", ctypes.c_double),
+        ("dso", ctypes.c_double), ("dsd", ctypes.c_double),
+        ("view_block", ctypes.POINTER(ctypes.c_int32)),
+    ]
+
+
+class GeometryInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64),
+        ("M", ctypes.c_int), ("N", ctypes.c_int), ("block_axis", ctypes.c_int),
+        ("max_views_per_block", ctypes.c_int), ("max_block_cols", ctypes.c_int64),
+    ]
+
+
+class SolveParamsC(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double), ("gamma", ctypes.c_double), ("epochs", ctypes.c_int),
+        ("step_rule", ctypes.c_int), ("mu", ctypes.c_double), ("rho", ctypes.c_double),
+        ("power_iters", ctypes.c_int), ("pair_sampling", ctypes.c_int), ("cells", ctypes.c_int),
+        ("n_cells", ctypes.c_int), ("tv_lambda", ctypes.c_double), ("tv_iters", ctypes.c_int),
+        ("storage", ctypes.c_int), ("seed", ctypes.c_uint64),
+    ]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [
+        ("residual_norm", ctypes.c_double), ("mu", ctypes.c_double),
+        ("iteration", ctypes.c_int64), ("epoch", ctypes.c_double), ("updates", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_LIB = None
+_vp, _i32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libbsgd.so (building it first if it is missing)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise BSGDError(3, "libbsgd.so not found at %s" % path)
+    lib = ctypes.CDLL(path)
+    st = ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "bsgd_last_error": (ctypes.c_char_p, []),
+        "bsgd_status_string": (ctypes.c_char_p, [st]),
+        "bsgd_geometry_create": (st, [P(GeometryDesc), ctypes.c_int, ctypes.c_int, P(_vp)]),
+        "bsgd_geometry_destroy": (st, [_vp]),
+        "bsgd_geometry_get_info": (st, [_vp, P(GeometryInfo)]),
+        "bsgd_geometry_pair_rays": (st, [_vp, ctypes.c_int, ctypes.c_int, P(ctypes.c_int64)]),
+        "bsgd_forward_project": (st, [_vp, _vp, st, _vp, st, _i32p, ctypes.c_int, _i32p,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
+        "bsgd_back_project": (st, [_vp, _vp, st, _vp, st, _i32p, ctypes.c_int, _i32p,
+                                   ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _vp]),
+        "bsgd_count_updates": (st, [_vp, _i32p, ctypes.c_int, _i32p, ctypes.c_int,
+                                    P(ctypes.c_int64), _vp]),
+        "bsgd_power_iteration": (st, [_vp, ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int,
+                                      P(ctypes.c_double), _vp]),
+        "bsgd_tv_prox": (st, [_vp, _vp, st, ctypes.c_double, ctypes.c_int, _vp]),
+        "bsgd_state_create": (st, [_vp, P(SolveParamsC), _vp, st, _vp, P(_vp)]),
+        "bsgd_state_destroy": (st, [_vp]),
+        "bsgd_block_step": (st, [_vp, _vp, ctypes.c_int, _vp]),
+        "bsgd_state_query": (st, [_vp, P(Report), _vp]),
+        "bsgd_trace_stride": (ctypes.c_int64, [_vp]),
+        "bsgd_state_read_trace": (st, [_vp, _i32p, ctypes.c_int64, ctypes.c_int64, _vp]),
+        "bsgd_state_set_replay": (st, [_vp, _i32p, ctypes.c_int64]),
+        "bsgd_state_profile": (st, [_vp, ctypes.c_int]),
+        "bsgd_state_read_profile": (st, [_vp, P(Profile), _vp]),
+        "bsgd_solve": (st, [_vp, P(SolveParamsC), _vp, st, _vp, st, P(Report), _vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        msg = load().bsgd_last_error()
+        raise BSGDError(status, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------------------
+# torch marshalling helpers (torch is imported lazily: the build and the CPU
+# tests do not need a GPU)
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    m = {torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+    if t.dtype not in m:
+        raise BSGDError(1, "unsupported dtype %s" % t.dtype)
+    return m[t.dtype]
+
+
+def _dev_ptr(t, what):
+    if not t.is_cuda:
+        raise BSGDError(1, "%s must be a CUDA tensor" % what)
+    if not t.is_contiguous():
+        raise BSGDError(1, "%s must be contiguous" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ids(ids):
+    if ids is None:
+        return None, 0, None
+    arr = np.ascontiguousarray(np.asarray(ids, dtype=np.int32).reshape(-1))
+    return arr.ctypes.data_as(_i32p), int(arr.size), arr
+
+
+# ---------------------------------------------------------------------------
+# Geometry
+
+class Geometry:
+    """Owning handle of a bsgd_geometry (bsgd_geometry_create / _destroy)."""
+
+    def __init__(self, kind, nx, ny, nz, dx, dy, dz, n_views, nu, nv, du, dv, dso=0.0, dsd=0.0,
+                 angles=None, view_block=None, M=1, N=1):
+        lib = load()
+        self.kind = kind
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.dx, self.dy, self.dz = float(dx), float(dy), float(dz)
+        self.n_views, self.nu, self.nv = int(n_views), int(nu), int(nv)
+        self.du, self.dv, self.dso, self.dsd = float(du), float(dv), float(dso), float(dsd)
+        self._angles = None if angles is None else np.ascontiguousarray(angles, dtype=np.float64)
+        self._vb = None if view_block is None else np.ascontiguousarray(view_block, dtype=np.int32)
+        d = GeometryDesc(KINDS[kind] if isinstance(kind, str) else int(kind), self.nx, self.ny,
+                         self.nz, self.dx, self.dy, self.dz, self.n_views,
+                         None if self._angles is None else self._angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         self.nu, self.nv, self.du, self.dv, self.dso, self.dsd,
+                         None if self._vb is None else self._vb.ctypes.data_as(_i32p))
+        h = ctypes.c_void_p()
+        _check(lib.bsgd_geometry_create(ctypes.byref(d), int(M), int(N), ctypes.byref(h)))
+        self.handle = h
+        info = GeometryInfo()
+        _check(lib.bsgd_geometry_get_info(h, ctypes.byref(info)))
+        self.info = info
+        self.M, self.N = info.M, info.N
+
+    @property
+    def n_rows(self):
+        return int(self.info.n_rows)
+
+    @property
+    def n_cols(self):
+        return int(self.info.n_cols)
+
+    @property
+    def vol_shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def sino_shape(self):
+        return (self.n_views, self.nv, self.nu)
+
+    def pair_rays(self, i, j) -> int:
+        out = ctypes.c_int64()
+        _check(load().bsgd_geometry_pair_rays(self.handle, int(i), int(j), ctypes.byref(out)))
+        return int(out.value)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _check(load().bsgd_geometry_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bsgd_geometry_create(**kw) -> Geometry:
+    return Geometry(**kw)
+
+
+def bsgd_forward_project(geom, x, y, row_blocks=None, col_blocks=None, accumulate=False,
+                         batch=1, stream=None):
+    rp, nr, _ra = _ids(row_blocks)
+    cp, nc, _ca = _ids(col_blocks)
+    _check(load().bsgd_forward_project(geom.handle, _dev_ptr(x, "x"), dtype_code(x),
+                                       _dev_ptr(y, "y"), dtype_code(y), rp, nr, cp, nc,
+                                       int(bool(accumulate)), int(batch), _stream(stream)))
+    return y
+
+
+def bsgd_back_project(geom, r, x, row_blocks=None, col_blocks=None, scale=1.0, accumulate=False,
+                      batch=1, stream=None):
+    rp, nr, _ra = _ids(row_blocks)
+    cp, nc, _ca = _ids(col_blocks)
+    _check(load().bsgd_back_project(geom.handle, _dev_ptr(r, "r"), dtype_code(r),
+                                    _dev_ptr(x, "x"), dtype_code(x), rp, nr, cp, nc,
+                                    float(scale), int(bool(accumulate)), int(batch),
+                                    _stream(stream)))
+    return x
+
+
+def bsgd_count_updates(geom, row_blocks=None, col_blocks=None, stream=None) -> int:
+    rp, nr, _ra = _ids(row_blocks)
+    cp, nc, _ca = _ids(col_blocks)
+    out = ctypes.c_int64()
+    _check(load().bsgd_count_updates(geom.handle, rp, nr, cp, nc, ctypes.byref(out),
+                                     _stream(stream)))
+    return int(out.value)
+
+
+def bsgd_power_iteration(geom, col_block, iters=30, row_blocks=None, stream=None) -> float:
+    rp, nr, _ra = _ids(row_blocks)
+    out = ctypes.c_double()
+    _check(load().bsgd_power_iteration(geom.handle, int(col_block), int(iters), rp, nr,
+                                       ctypes.byref(out), _stream(stream)))
+    return float(out.value)
+
+
+def bsgd_tv_prox(geom, x, kappa, iters=20, stream=None):
+    _check(load().bsgd_tv_prox(geom.handle, _dev_ptr(x, "x"), dtype_code(x), float(kappa),
+                               int(iters), _stream(stream)))
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Solver
+
+@dataclass
+class SolveParams:
+    alpha: float
+    gamma: float
+    epochs: int = 1
+    step_rule: int = STEP_STRIP
+    mu: float = 0.0
+    rho: float = 0.25
+    power_iters: int = 30
+    pair_sampling: int = PAIRS_UNIFORM
+    cells: int = CELLS_NONE
+    n_cells: int = 1
+    tv_lambda: float = 0.0
+    tv_iters: int = 20
+    storage: int = F32
+    seed: int = 1
+
+    def c(self):
+        return SolveParamsC(self.alpha, self.gamma, self.epochs, self.step_rule, self.mu, self.rho,
+                            self.power_iters, self.pair_sampling, self.cells, self.n_cells,
+                            self.tv_lambda, self.tv_iters, self.storage, self.seed)
+
+
+class State:
+    """Owning handle of a bsgd_state."""
+
+    def __init__(self, geom, params: SolveParams, y, stream=None):
+        self.geom, self.params = geom, params
+        self._pc = params.c()
+        h = ctypes.c_void_p()
+        _check(load().bsgd_state_create(geom.handle, ctypes.byref(self._pc), _dev_ptr(y, "y"),
+                                        dtype_code(y), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def block_step(self, x, n_iters, stream=None):
+        _check(load().bsgd_block_step(self.handle, _dev_ptr(x, "x"), int(n_iters), _stream(stream)))
+        return x
+
+    def query(self, stream=None) -> dict:
+        rep = Report()
+        _check(load().bsgd_state_query(self.handle, ctypes.byref(rep), _stream(stream)))
+        return rep.as_dict()
+
+    @property
+    def trace_stride(self) -> int:
+        return int(load().bsgd_trace_stride(self.handle))
+
+    def read_trace(self, n_iters, stream=None) -> np.ndarray:
+        s = self.trace_stride
+        buf = np.zeros(max(1, n_iters * s), dtype=np.int32)
+        _check(load().bsgd_state_read_trace(self.handle, buf.ctypes.data_as(_i32p), buf.size,
+                                            int(n_iters), _stream(stream)))
+        return buf[: n_iters * s].reshape(n_iters, s)
+
+    def set_replay(self, trace: np.ndarray):
+        t = np.ascontiguousarray(trace, dtype=np.int32)
+        n = 0 if t.size == 0 else t.shape[0]
+        _check(load().bsgd_state_set_replay(self.handle, t.ctypes.data_as(_i32p), int(n)))
+
+    def profile(self, enable=True):
+        _check(load().bsgd_state_profile(self.handle, int(bool(enable))))
+
+    def read_profile(self, stream=None) -> dict:
+        pr = Profile()
+        _check(load().bsgd_state_read_profile(self.handle, ctypes.byref(pr), _stream(stream)))
+        return {name: {"launches": int(pr.launches[k]), "ms": float(pr.ms[k])}
+                for k, name in enumerate(STAGES)}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _check(load().bsgd_state_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def bsgd_state_create(geom, params, y, stream=None) -> State:
+    return State(geom, params, y, stream)
+
+
+def bsgd_block_step(state: State, x, n_iters, stream=None):
+    return state.block_step(x, n_iters, stream)
+
+
+def bsgd_state_query(state: State, stream=None) -> dict:
+    return state.query(stream)
+
+
+def _any_ptr(t):
+    """Device pointer for CUDA tensors, host pointer for CPU tensors / arrays."""
+    if isinstance(t, np.ndarray):
+        if not t.flags.c_contiguous:
+            raise BSGDError(1, "array must be C-contiguous")
+        return ctypes.c_void_p(t.ctypes.data)
+    if not t.is_contiguous():
+        raise BSGDError(1, "tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _any_dtype(t):
+    if isinstance(t, np.ndarray):
+        if t.dtype == np.float32:
+            return F32
+        if t.dtype == np.float16:
+            return F16
+        raise BSGDError(1, "numpy arrays must be float32 or float16")
+    return dtype_code(t)
+
+
+def bsgd_solve(geom, params: SolveParams, y, x, stream=None) -> dict:
+    """One-call reconstruction; y and x may live on the host or the device."""
+    pc = params.c()
+    rep = Report()
+    _check(load().bsgd_solve(geom.handle, ctypes.byref(pc), _any_ptr(y), _any_dtype(y),
+                             _any_ptr(x), _any_dtype(x), ctypes.byref(rep), _stream(stream)))
+    return rep.as_dict()

@@ -1,0 +1,202 @@
+// Internal declarations of the BSGD library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bsgd.h"
+
+namespace bsgd {
+
+// ---------------------------------------------------------------------------
+// Error reporting
+
+void set_error(const std::string &msg);
+bsgd_status fail(bsgd_status s, const std::string &msg);
+bsgd_status cuda_fail(cudaError_t e, const char *what);
+
+#define BSGD_CUDA(call)                                                    \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return ::bsgd::cuda_fail(e_, #call);        \
+    } while (0)
+
+#define BSGD_TRY(call)                                                     \
+    do {                                                                   \
+        bsgd_status s_ = (call);                                           \
+        if (s_ != BSGD_OK) return s_;                                      \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Geometry tables (built on the host in FP64, stored in FP32 on the device)
+
+// Ray of pixel (u, v) at one view, in voxel units relative to the volume's low
+// corner: start = p0 + u * pu, end = c0 + u * cu + v * cv. For divergent beams
+// the start is the source (pu = 0); for parallel beams both ends move with u.
+struct ViewRay {
+    float p0[3];
+    float pu[3];
+    float c0[3];
+    float cu[3];
+    float cv[3];
+    float pad;
+};
+static_assert(sizeof(ViewRay) == 64, "ViewRay is 4 x float4");
+
+// Detector rectangle [u0, u1] x [v0, v1] (inclusive; empty when u0 > u1).
+struct Band {
+    int u0, u1, v0, v1;
+};
+
+constexpr int kMaxPairs = 64;  // pairs per iteration the work list can hold
+
+struct DeviceGeom {
+    const ViewRay *rays;       // n_views
+    const Band *bands;         // n_views x (N + 1); entry N = whole volume
+    const int *block_views;    // M x max_views (padded with -1)
+    const int *block_nviews;   // M
+    const int *plane_start;    // N + 1 planes along the block axis
+    const int *view_block;     // n_views
+    int nx, ny, nz;
+    float hx, hy, hz;
+    int nu, nv, n_views;
+    int M, N, axis, max_views;
+    int64_t n_rows, n_cols;
+    int plane_stride;          // voxels per plane along the block axis
+};
+
+}  // namespace bsgd
+
+struct bsgd_geometry {
+    bsgd_geometry_desc desc;   // angles / view_block point into the vectors below
+    std::vector<double> angles;
+    std::vector<int32_t> view_block;
+    int M = 0, N = 0;
+    int axis = 2;              // block axis: 1 = y, 2 = z
+    int n_planes = 0;          // planes along the block axis
+    std::vector<int> plane_start;               // N + 1
+    std::vector<std::vector<int>> block_views;  // M lists
+    int max_views = 0;
+    std::vector<bsgd::ViewRay> rays;
+    std::vector<bsgd::Band> bands;              // n_views x (N + 1), traversal bands
+    std::vector<int> wband;                     // M x N x 2: exact v-band of the pair
+    int device = 0;
+    // device copies
+    bsgd::ViewRay *d_rays = nullptr;
+    bsgd::Band *d_bands = nullptr;
+    int *d_block_views = nullptr;
+    int *d_block_nviews = nullptr;
+    int *d_plane_start = nullptr;
+    int *d_view_block = nullptr;
+    bsgd::DeviceGeom dg{};
+
+    int64_t n_rows() const { return (int64_t)desc.n_views * desc.nv * desc.nu; }
+    int64_t n_cols() const { return (int64_t)desc.nx * desc.ny * desc.nz; }
+    int64_t block_cols(int j) const {
+        return (int64_t)(plane_start[j + 1] - plane_start[j]) * dg.plane_stride;
+    }
+};
+
+namespace bsgd {
+
+// ---------------------------------------------------------------------------
+// Projector launches (siddon.cu)
+
+enum TraceMode : int {
+    kFpPlain = 0,   // y = (y or 0) + A x
+    kBpPlain = 1,   // x += scale A^T r
+    kCount = 2,     // number of positive-length segments
+};
+
+struct PlainLaunch {
+    const int *row_ids;  // host list of selected row-block ids
+    int n_rb;
+    int j0, j1;          // column blocks [j0, j1)
+    int unused;
+};
+
+// Tiles of the largest band of these views for column blocks [j0, j1) (host
+// side, from the geometry tables).
+int tiles_for(const bsgd_geometry *g, const std::vector<int> &views, int j0, int j1, int tile_u,
+              int tile_v);
+
+bsgd_status launch_fp_plain(const bsgd_geometry *g, const PlainLaunch &L, const void *x,
+                            bsgd_dtype xt, void *y, bsgd_dtype yt, int accumulate,
+                            cudaStream_t st);
+bsgd_status launch_bp_plain(const bsgd_geometry *g, const PlainLaunch &L, const void *r,
+                            bsgd_dtype rt, float *x, float scale, cudaStream_t st);
+bsgd_status launch_count(const bsgd_geometry *g, const PlainLaunch &L,
+                         unsigned long long *d_count, cudaStream_t st);
+// Clear the rows of every view of the listed row blocks.
+bsgd_status zero_rows(const bsgd_geometry *g, const int *row_ids, int n_rb, void *y,
+                      bsgd_dtype yt, cudaStream_t st);
+
+// Tile of rays per CTA.
+constexpr int kTileU3 = 16, kTileV3 = 8;   // 3D: 2 x 2 warps of 8 u x 4 v rays
+constexpr int kTileU2 = 128, kTileV2 = 1;  // 2D: 4 warps of 32 u rays
+inline int tile_u(const bsgd_geometry *g) { return g->desc.nv > 1 ? kTileU3 : kTileU2; }
+inline int tile_v(const bsgd_geometry *g) { return g->desc.nv > 1 ? kTileV3 : kTileV2; }
+
+// ---------------------------------------------------------------------------
+// Small device helpers shared by host launchers
+
+bsgd_status upload(void **dst, const void *src, size_t bytes);
+size_t dtype_size(bsgd_dtype t);
+bool dtype_ok(int t);
+
+}  // namespace bsgd
+
+namespace bsgd {
+
+// ---------------------------------------------------------------------------
+// Solver state shared by the solver kernels
+
+// Device work list of one iteration, written by the sampler.
+struct Work {
+    int n_pairs;
+    int pair_i[kMaxPairs], pair_j[kMaxPairs];
+    int n_cols;                 // distinct column blocks of the pairs
+    int cols[kMaxPairs];
+    int n_rows;                 // distinct row blocks of the pairs
+    int rows[kMaxPairs];
+};
+
+struct SolveDev {
+    const void *y;     // n_rows, storage type
+    void *z;           // N x n_rows, z^j (last FP of column block j)
+    void *rt;          // N x n_rows, residual snapshots r~^j
+    void *r;           // n_rows, r = y - sum_j z^j
+    float *g;          // n_cols, aggregated gradient
+    double *S;         // M x nv: sum over the row block's views and u of r^2
+    const Work *work;
+    const int *cells;  // kMaxPairs x max_views chosen cells (-1: whole view)
+    int n_cells;       // 1 (no cells), 2 or 4
+    const double *mu;  // step
+};
+
+// Sub-detector cell rectangle (Fig. 2): halves in u for 2 cells, quadrants
+// (v half * 2 + u half) for 4.
+__host__ __device__ inline void cell_rect(int nu, int nv, int n_cells, int c, Band &b) {
+    if (n_cells <= 1 || c < 0) return;
+    const int uh = c & 1, vh = n_cells == 4 ? (c >> 1) : 0;
+    const int um = nu / 2, vm = nv / 2;
+    if (uh) b.u0 = max(b.u0, um); else b.u1 = min(b.u1, um - 1);
+    if (n_cells == 4) {
+        if (vh) b.v0 = max(b.v0, vm); else b.v1 = min(b.v1, vm - 1);
+    }
+}
+
+bsgd_status launch_fp_solve(const bsgd_geometry *g, const SolveDev &S, const void *x,
+                            bsgd_dtype st_t, int max_pairs, int max_tiles, bool fused,
+                            cudaStream_t st);
+bsgd_status launch_bp_solve(const bsgd_geometry *g, const SolveDev &S, bsgd_dtype st_t,
+                            int max_pairs, int max_tiles, cudaStream_t st);
+bsgd_status launch_count_cells(const bsgd_geometry *g, int j, int n_cells,
+                               unsigned long long *d_counts, cudaStream_t st);
+
+}  // namespace bsgd

@@ -1,0 +1,351 @@
+// Siddon projector kernels: plain FP / BP / segment count over selected blocks,
+// and the two solver kernels of one BSGD iteration (FP with the fused residual
+// update, BP of the residual change).
+//
+// Grid: x = tile of the detector band (128 rays per CTA), y = view slot inside
+// the selected row block(s), z = pair slot (solver). A CTA's rays all belong to
+// one view and one column block, so they share the view's ray table entry and
+// walk a compact bundle of neighbouring voxels.
+#include "siddon_device.cuh"
+
+namespace bsgd {
+
+// Selected row blocks of a plain launch (views = block_views of each).
+struct RowSel {
+    int n;
+    int ids[64];
+};
+
+__device__ __forceinline__ int sel_view(const DeviceGeom &G, const RowSel &R, int slot) {
+    const int k = slot / G.max_views, pos = slot % G.max_views;
+    if (k >= R.n) return -1;
+    const int i = R.ids[k];
+    return pos < G.block_nviews[i] ? G.block_views[i * G.max_views + pos] : -1;
+}
+
+// ---------------------------------------------------------------------------
+// Plain kernels
+
+template <bool k3D, typename TX, typename TY>
+__global__ void __launch_bounds__(128) fp_plain_kernel(const DeviceGeom G, const RowSel R, int j0,
+                                                       int j1, const TX *__restrict__ x,
+                                                       TY *__restrict__ y) {
+    const int a = sel_view(G, R, blockIdx.y);
+    if (a < 0) return;
+    const Band b = band_of(G, a, j0, j1);
+    int u, v, nt;
+    if (!tile_pixel<k3D>(b, blockIdx.x, u, v, nt)) return;
+    RayWalk w;
+    float acc = 0.f;
+    if (ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w)) {
+        ray_walk(w, [&](int idx, float s) { acc = fmaf(s, ldf(x + idx), acc); });
+        acc *= w.L;
+    }
+    const int64_t row = ((int64_t)a * G.nv + v) * G.nu + u;
+    stf(y + row, ldv(y + row) + acc);
+}
+
+template <bool k3D, typename TR>
+__global__ void __launch_bounds__(128) bp_plain_kernel(const DeviceGeom G, const RowSel R, int j0,
+                                                       int j1, const TR *__restrict__ r,
+                                                       float *__restrict__ x, float scale) {
+    const int a = sel_view(G, R, blockIdx.y);
+    if (a < 0) return;
+    const Band b = band_of(G, a, j0, j1);
+    int u, v, nt;
+    if (!tile_pixel<k3D>(b, blockIdx.x, u, v, nt)) return;
+    const int64_t row = ((int64_t)a * G.nv + v) * G.nu + u;
+    const float rv = ldf(r + row) * scale;
+    if (rv == 0.f) return;
+    RayWalk w;
+    if (!ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w)) return;
+    const float wl = rv * w.L;
+    ray_walk(w, [&](int idx, float s) {
+        if (s > 0.f) atomicAdd(x + idx, s * wl);
+    });
+}
+
+// Voxel-ray updates (segments longer than 1e-4 of the smallest voxel edge),
+// accumulated per (view, cell) into counts.
+template <bool k3D>
+__global__ void __launch_bounds__(128) count_kernel(const DeviceGeom G, const RowSel R, int j0,
+                                                    int j1, int n_cells,
+                                                    unsigned long long *__restrict__ counts) {
+    const int a = sel_view(G, R, blockIdx.y);
+    if (a < 0) return;
+    const Band b = band_of(G, a, j0, j1);
+    int u, v, nt;
+    if (!tile_pixel<k3D>(b, blockIdx.x, u, v, nt)) return;
+    RayWalk w;
+    unsigned long long c = 0;
+    if (ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w)) {
+        // pieces shorter than 1e-4 of the smallest voxel edge are edge / corner
+        // crossings (zero length in exact arithmetic) and are not counted
+        const float eps = 1e-4f * fminf(G.hx, fminf(G.hy, G.hz)) / w.L;
+        ray_walk(w, [&](int, float s) { c += s > eps ? 1ull : 0ull; });
+    }
+    if (c == 0) return;
+    int cell = 0;
+    if (n_cells == 2) cell = u >= G.nu / 2;
+    if (n_cells == 4) cell = (v >= G.nv / 2) * 2 + (u >= G.nu / 2);
+    atomicAdd(counts + (size_t)a * n_cells + cell, c);
+}
+
+__global__ void zero_views_kernel(const DeviceGeom G, const RowSel R, void *y, int esize) {
+    const int a = sel_view(G, R, blockIdx.y);
+    if (a < 0) return;
+    const int64_t per = (int64_t)G.nv * G.nu;
+    char *base = reinterpret_cast<char *>(y) + (size_t)a * per * esize;
+    const int64_t nbytes = per * esize;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4; k < nbytes;
+         k += (int64_t)gridDim.x * blockDim.x * 4) {
+        if (k + 4 <= nbytes && ((reinterpret_cast<uintptr_t>(base + k) & 3) == 0))
+            *reinterpret_cast<uint32_t *>(base + k) = 0u;
+        else
+            for (int t = 0; t < 4 && k + t < nbytes; ++t) base[k + t] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Solver kernels
+
+template <typename T>
+__device__ __forceinline__ bool solve_pixel(const DeviceGeom &G, const SolveDev &S, int &a, int &i,
+                                            int &j, int &u, int &v, bool &in_band) {
+    const Work &W = *S.work;
+    const int p = blockIdx.z;
+    if (p >= W.n_pairs) return false;
+    i = W.pair_i[p];
+    j = W.pair_j[p];
+    const int slot = blockIdx.y;
+    if (slot >= G.block_nviews[i]) return false;
+    a = G.block_views[i * G.max_views + slot];
+    Band b = G.bands[(size_t)a * (G.N + 1) + j];
+    if (S.n_cells > 1) cell_rect(G.nu, G.nv, S.n_cells, S.cells[p * G.max_views + slot], b);
+    int nt;
+    in_band = G.nv > 1 ? tile_pixel<true>(b, blockIdx.x, u, v, nt)
+                       : tile_pixel<false>(b, blockIdx.x, u, v, nt);
+    return (int)blockIdx.x < nt;
+}
+
+// FP of the pair's rows: z_new = A_R^J x_J; with FUSED also
+// z^J = z_new, r = y - sum_j z^j and the FP64 row-block residual sums S.
+template <typename T, bool FUSED>
+__global__ void __launch_bounds__(128) fp_solve_kernel(const DeviceGeom G, const SolveDev S,
+                                                       const T *__restrict__ x) {
+    int a, i, j, u, v;
+    bool act;
+    if (!solve_pixel<T>(G, S, a, i, j, u, v, act)) return;
+    float zn = 0.f;
+    if (act) {
+        RayWalk w;
+        if (ray_setup(G, a, u, v, G.plane_start[j], G.plane_start[j + 1], w)) {
+            float acc = 0.f;
+            ray_walk(w, [&](int idx, float s) { acc = fmaf(s, ldf(x + idx), acc); });
+            zn = acc * w.L;
+        }
+    }
+    const int64_t row = act ? ((int64_t)a * G.nv + v) * G.nu + u : 0;
+    T *z = reinterpret_cast<T *>(S.z);
+    if (!FUSED) {
+        if (act) stf(z + (int64_t)j * G.n_rows + row, zn);
+        return;
+    }
+    double dn = 0.0;
+    if (act) {
+        stf(z + (int64_t)j * G.n_rows + row, zn);
+        zn = rnd(zn, z);
+        float zs = 0.f;
+        for (int jj = 0; jj < G.N; ++jj) zs += jj == j ? zn : ldv(z + (int64_t)jj * G.n_rows + row);
+        T *r = reinterpret_cast<T *>(S.r);
+        const float rn = rnd(ldf(reinterpret_cast<const T *>(S.y) + row) - zs, r);
+        const float ro = ldv(r + row);
+        stf(r + row, rn);
+        dn = (double)rn * rn - (double)ro * ro;
+    }
+    // lanes of one detector row: 8 (3D tile) or 32 (2D tile); the group's first
+    // lane has the lowest u, so it is active whenever any lane of the group is
+    const int group = G.nv > 1 ? 8 : 32;
+    for (int o = group / 2; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+    if ((threadIdx.x & (group - 1)) == 0 && act && dn != 0.0)
+        atomicAdd(S.S + (size_t)i * G.nv + v, dn);
+}
+
+// BP of the residual change of the pair's rows into g_J; r~^J = r.
+template <typename T>
+__global__ void __launch_bounds__(128) bp_solve_kernel(const DeviceGeom G, const SolveDev S) {
+    int a, i, j, u, v;
+    bool act;
+    if (!solve_pixel<T>(G, S, a, i, j, u, v, act) || !act) return;
+    const int64_t row = ((int64_t)a * G.nv + v) * G.nu + u;
+    const T *r = reinterpret_cast<const T *>(S.r);
+    T *rt = reinterpret_cast<T *>(S.rt) + (int64_t)j * G.n_rows;
+    const float rv = ldv(r + row), ro = ldv(rt + row);
+    stf(rt + row, rv);
+    const float dw = rv - ro;
+    if (dw == 0.f) return;
+    RayWalk w;
+    if (!ray_setup(G, a, u, v, G.plane_start[j], G.plane_start[j + 1], w)) return;
+    const float wl = dw * w.L;
+    float *gg = S.g;
+    ray_walk(w, [&](int idx, float s) {
+        if (s > 0.f) atomicAdd(gg + idx, s * wl);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+
+namespace {
+
+RowSel all_rows(const bsgd_geometry *g) {
+    RowSel R{};
+    R.n = g->M;
+    for (int i = 0; i < g->M && i < 64; ++i) R.ids[i] = i;
+    return R;
+}
+
+template <typename F>
+bsgd_status for_row_chunks(const bsgd_geometry *g, const PlainLaunch &L, F &&f) {
+    // row-block ids in chunks of 64 per launch
+    (void)g;
+    RowSel R{};
+    int k = 0;
+    for (int t = 0; t < L.n_rb; ++t) {
+        R.ids[k++] = L.row_ids[t];
+        if (k == 64 || t == L.n_rb - 1) {
+            R.n = k;
+            BSGD_TRY(f(R));
+            k = 0;
+        }
+    }
+    return BSGD_OK;
+}
+
+std::vector<int> views_of(const bsgd_geometry *g, const RowSel &R) {
+    std::vector<int> v;
+    for (int k = 0; k < R.n; ++k)
+        for (int a : g->block_views[R.ids[k]]) v.push_back(a);
+    return v;
+}
+
+template <typename TX, typename TY>
+void fp_plain_go(const bsgd_geometry *g, dim3 grid, const RowSel &R, int j0, int j1, const void *x,
+                 void *y, cudaStream_t st) {
+    if (g->desc.nv > 1)
+        fp_plain_kernel<true, TX, TY><<<grid, 128, 0, st>>>(g->dg, R, j0, j1, (const TX *)x, (TY *)y);
+    else
+        fp_plain_kernel<false, TX, TY><<<grid, 128, 0, st>>>(g->dg, R, j0, j1, (const TX *)x, (TY *)y);
+}
+
+template <typename TX>
+void fp_plain_y(const bsgd_geometry *g, dim3 grid, const RowSel &R, int j0, int j1, const void *x,
+                void *y, bsgd_dtype yt, cudaStream_t st) {
+    if (yt == BSGD_F32) fp_plain_go<TX, float>(g, grid, R, j0, j1, x, y, st);
+    else if (yt == BSGD_BF16) fp_plain_go<TX, __nv_bfloat16>(g, grid, R, j0, j1, x, y, st);
+    else fp_plain_go<TX, __half>(g, grid, R, j0, j1, x, y, st);
+}
+
+}  // namespace
+
+bsgd_status zero_rows(const bsgd_geometry *g, const int *row_ids, int n_rb, void *y,
+                      bsgd_dtype yt, cudaStream_t st) {
+    PlainLaunch L{row_ids, n_rb, 0, g->N, 0};
+    return for_row_chunks(g, L, [&](const RowSel &R) -> bsgd_status {
+        dim3 grid(std::max(1, (int)std::min<int64_t>(64, ((int64_t)g->desc.nu * g->desc.nv * 2 + 511) / 512)),
+                  R.n * g->max_views);
+        zero_views_kernel<<<grid, 128, 0, st>>>(g->dg, R, y, (int)dtype_size(yt));
+        BSGD_CUDA(cudaGetLastError());
+        return BSGD_OK;
+    });
+}
+
+bsgd_status launch_fp_plain(const bsgd_geometry *g, const PlainLaunch &L, const void *x,
+                            bsgd_dtype xt, void *y, bsgd_dtype yt, int accumulate,
+                            cudaStream_t st) {
+    (void)accumulate;
+    return for_row_chunks(g, L, [&](const RowSel &R) -> bsgd_status {
+        const int tiles = tiles_for(g, views_of(g, R), L.j0, L.j1, tile_u(g), tile_v(g));
+        if (tiles == 0) return BSGD_OK;
+        dim3 grid(tiles, R.n * g->max_views);
+        if (xt == BSGD_F32) fp_plain_y<float>(g, grid, R, L.j0, L.j1, x, y, yt, st);
+        else if (xt == BSGD_BF16) fp_plain_y<__nv_bfloat16>(g, grid, R, L.j0, L.j1, x, y, yt, st);
+        else fp_plain_y<__half>(g, grid, R, L.j0, L.j1, x, y, yt, st);
+        BSGD_CUDA(cudaGetLastError());
+        return BSGD_OK;
+    });
+}
+
+bsgd_status launch_bp_plain(const bsgd_geometry *g, const PlainLaunch &L, const void *r,
+                            bsgd_dtype rt, float *x, float scale, cudaStream_t st) {
+    return for_row_chunks(g, L, [&](const RowSel &R) -> bsgd_status {
+        const int tiles = tiles_for(g, views_of(g, R), L.j0, L.j1, tile_u(g), tile_v(g));
+        if (tiles == 0) return BSGD_OK;
+        dim3 grid(tiles, R.n * g->max_views);
+        const bool t3 = g->desc.nv > 1;
+#define BP_GO(T)                                                                                   \
+    if (t3) bp_plain_kernel<true, T><<<grid, 128, 0, st>>>(g->dg, R, L.j0, L.j1, (const T *)r, x, scale); \
+    else bp_plain_kernel<false, T><<<grid, 128, 0, st>>>(g->dg, R, L.j0, L.j1, (const T *)r, x, scale);
+        if (rt == BSGD_F32) { BP_GO(float) }
+        else if (rt == BSGD_BF16) { BP_GO(__nv_bfloat16) }
+        else { BP_GO(__half) }
+#undef BP_GO
+        BSGD_CUDA(cudaGetLastError());
+        return BSGD_OK;
+    });
+}
+
+bsgd_status launch_count(const bsgd_geometry *g, const PlainLaunch &L,
+                         unsigned long long *d_counts, cudaStream_t st) {
+    return for_row_chunks(g, L, [&](const RowSel &R) -> bsgd_status {
+        const int tiles = tiles_for(g, views_of(g, R), L.j0, L.j1, tile_u(g), tile_v(g));
+        if (tiles == 0) return BSGD_OK;
+        dim3 grid(tiles, R.n * g->max_views);
+        if (g->desc.nv > 1) count_kernel<true><<<grid, 128, 0, st>>>(g->dg, R, L.j0, L.j1, 1, d_counts);
+        else count_kernel<false><<<grid, 128, 0, st>>>(g->dg, R, L.j0, L.j1, 1, d_counts);
+        BSGD_CUDA(cudaGetLastError());
+        return BSGD_OK;
+    });
+}
+
+bsgd_status launch_count_cells(const bsgd_geometry *g, int j, int n_cells,
+                               unsigned long long *d_counts, cudaStream_t st) {
+    const RowSel R = all_rows(g);
+    std::vector<int> all(g->desc.n_views);
+    for (int a = 0; a < g->desc.n_views; ++a) all[a] = a;
+    const int tiles = tiles_for(g, all, j, j + 1, tile_u(g), tile_v(g));
+    if (tiles == 0) return BSGD_OK;
+    if (g->M > 64) return fail(BSGD_ERR_INVALID_ARG, "M > 64 not supported by the counter");
+    dim3 grid(tiles, R.n * g->max_views);
+    if (g->desc.nv > 1) count_kernel<true><<<grid, 128, 0, st>>>(g->dg, R, j, j + 1, n_cells, d_counts);
+    else count_kernel<false><<<grid, 128, 0, st>>>(g->dg, R, j, j + 1, n_cells, d_counts);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+bsgd_status launch_fp_solve(const bsgd_geometry *g, const SolveDev &S, const void *x,
+                            bsgd_dtype st_t, int max_pairs, int max_tiles, bool fused,
+                            cudaStream_t st) {
+    dim3 grid(max_tiles, g->max_views, max_pairs);
+#define FPS_GO(T)                                                                          \
+    if (fused) fp_solve_kernel<T, true><<<grid, 128, 0, st>>>(g->dg, S, (const T *)x);     \
+    else fp_solve_kernel<T, false><<<grid, 128, 0, st>>>(g->dg, S, (const T *)x);
+    if (st_t == BSGD_F32) { FPS_GO(float) }
+    else if (st_t == BSGD_BF16) { FPS_GO(__nv_bfloat16) }
+    else { FPS_GO(__half) }
+#undef FPS_GO
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+bsgd_status launch_bp_solve(const bsgd_geometry *g, const SolveDev &S, bsgd_dtype st_t,
+                            int max_pairs, int max_tiles, cudaStream_t st) {
+    dim3 grid(max_tiles, g->max_views, max_pairs);
+    if (st_t == BSGD_F32) bp_solve_kernel<float><<<grid, 128, 0, st>>>(g->dg, S);
+    else if (st_t == BSGD_BF16) bp_solve_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(g->dg, S);
+    else bp_solve_kernel<__half><<<grid, 128, 0, st>>>(g->dg, S);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+}  // namespace bsgd

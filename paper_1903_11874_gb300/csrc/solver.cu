@@ -1,0 +1,945 @@
+// BSGD solver state and the per-iteration kernels other than the projector:
+// block sampling, residual recomputation, the block step, FP64 residual-norm
+// tables and the power-iteration step size.
+//
+// One iteration (Algorithm 1; Algorithm 2 with sub-detector cells):
+//   sample_kernel     picks the pairs (i, j) (and cells) on the device
+//   fp_solve_kernel   z^j_R = A_R^J x_J, r_R = y_R - sum_j z^j_R   (siddon.cu)
+//   residual_kernel   only when several column blocks share a row block
+//   bp_solve_kernel   g_J += (A_R^J)^T (r_R - r~^J_R), r~^J_R = r_R (siddon.cu)
+//   update_kernel     x_J += mu g_J
+// The snapshot r~^J equals keeping Algorithm 1's memory g-hat^i: it stores the
+// residual the last BP of (i, J) used, so the BP of the change replaces
+// g-hat^i_J by the new one exactly.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "siddon_device.cuh"
+
+namespace bsgd {
+
+// ---------------------------------------------------------------------------
+// SplitMix64 counter spec (Steele, Lea and Flood 2014): draw number
+// n = it * 2^20 + lane + 1 of the generator seeded with `seed` is
+// mix(seed + n * 0x9E3779B97F4A7C15); u = (draw >> 11) * 2^-53.
+
+constexpr int kLaneRows = 0, kLaneCols = 256, kLanePair = 1024, kLaneCells = 2048;
+constexpr double kResidualFloor = 1e-9;
+constexpr double kCellFloor = 1e-12;
+
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ inline double draw_u(uint64_t seed, int64_t it, int lane) {
+    const uint64_t n = ((uint64_t)it << 20) + (uint64_t)lane + 1ull;
+    return (double)(mix64(seed + n * 0x9E3779B97F4A7C15ull) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// smallest index whose running FP64 sum exceeds u * total
+__device__ inline int pick_weighted(double u, const double *w, int n, int stride) {
+    double tot = 0.0;
+    for (int k = 0; k < n; ++k) tot += w[k * stride];
+    const double c = u * tot;
+    double acc = 0.0;
+    int last = 0;
+    for (int k = 0; k < n; ++k) {
+        acc += w[k * stride];
+        if (w[k * stride] > 0.0) last = k;
+        if (acc > c) return k;
+    }
+    return last;
+}
+
+struct SampleArgs {
+    DeviceGeom G;
+    Work *work;
+    int *cells;                 // kMaxPairs x max_views
+    int64_t *iter;
+    uint64_t seed;
+    int pairs_mode, cells_mode, n_cells, kM, kN;
+    const double *S;            // M x nv
+    const int *wband;           // M x N x 2
+    const double *cw;           // N x n_views x n_cells
+    const int32_t *replay;      // replay_n x stride
+    int64_t replay_start, replay_n;
+    int32_t *trace;             // trace_cap x stride
+    int64_t trace_cap;
+    int stride;
+    const unsigned long long *counts;  // N x n_views x n_cells
+    unsigned long long *updates;
+};
+
+constexpr int kSampleThreads = 128;
+constexpr int kMaxSampleBlocks = 1024;
+
+__global__ void __launch_bounds__(kSampleThreads) sample_kernel(const SampleArgs A) {
+    __shared__ int s_rows[kMaxSampleBlocks], s_cols[kMaxSampleBlocks];
+    __shared__ double s_w[kMaxPairs * 64];
+    __shared__ int s_np;
+    __shared__ int s_pi[kMaxPairs], s_pj[kMaxPairs];
+    const DeviceGeom &G = A.G;
+    const int64_t it = *A.iter;
+    const int tid = threadIdx.x;
+    const bool replay = A.replay && it >= A.replay_start && it - A.replay_start < A.replay_n;
+    const int32_t *rep = replay ? A.replay + (it - A.replay_start) * A.stride : nullptr;
+
+    if (replay) {
+        if (tid == 0) {
+            s_np = rep[0];
+            for (int p = 0; p < s_np; ++p) {
+                s_pi[p] = rep[1 + 2 * p];
+                s_pj[p] = rep[2 + 2 * p];
+            }
+        }
+    } else if (A.pairs_mode == BSGD_PAIRS_UNIFORM) {
+        if (tid == 0) {
+            for (int k = 0; k < G.M; ++k) s_rows[k] = k;
+            for (int t = 0; t < A.kM; ++t) {  // partial Fisher-Yates
+                const int idx = t + (int)(draw_u(A.seed, it, kLaneRows + t) * (G.M - t));
+                const int tmp = s_rows[t]; s_rows[t] = s_rows[idx]; s_rows[idx] = tmp;
+            }
+            for (int k = 0; k < G.N; ++k) s_cols[k] = k;
+            for (int t = 0; t < A.kN; ++t) {
+                const int idx = t + (int)(draw_u(A.seed, it, kLaneCols + t) * (G.N - t));
+                const int tmp = s_cols[t]; s_cols[t] = s_cols[idx]; s_cols[idx] = tmp;
+            }
+            // sort the chosen prefixes (insertion sort; k is small)
+            for (int a = 1; a < A.kM; ++a)
+                for (int b = a; b > 0 && s_rows[b - 1] > s_rows[b]; --b) {
+                    const int t = s_rows[b]; s_rows[b] = s_rows[b - 1]; s_rows[b - 1] = t;
+                }
+            for (int a = 1; a < A.kN; ++a)
+                for (int b = a; b > 0 && s_cols[b - 1] > s_cols[b]; --b) {
+                    const int t = s_cols[b]; s_cols[b] = s_cols[b - 1]; s_cols[b - 1] = t;
+                }
+            int np = 0;
+            for (int a = 0; a < A.kM; ++a)
+                for (int b = 0; b < A.kN; ++b) {
+                    s_pi[np] = s_rows[a];
+                    s_pj[np] = s_cols[b];
+                    ++np;
+                }
+            s_np = np;
+        }
+    } else {  // residual-weighted pair: W_ij = sum_{v in R_ij} S[i][v] + floor
+        const int MN = G.M * G.N;
+        for (int k = tid; k < MN; k += blockDim.x) {
+            const int i = k / G.N;
+            const int lo = A.wband[2 * k], hi = A.wband[2 * k + 1];
+            double w = 0.0;
+            for (int v = lo; v <= hi; ++v) w += A.S[(size_t)i * G.nv + v];
+            s_w[k] = w;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int k = 0; k < MN; ++k) tot += s_w[k];
+            const double fl = kResidualFloor * tot / MN + 1e-300;
+            for (int k = 0; k < MN; ++k) s_w[k] += fl;
+            const int k = pick_weighted(draw_u(A.seed, it, kLanePair), s_w, MN, 1);
+            s_np = 1;
+            s_pi[0] = k / G.N;
+            s_pj[0] = k % G.N;
+        }
+    }
+    __syncthreads();
+    const int np = s_np;
+    // cells: one per view of each pair's row block
+    for (int q = tid; q < np * G.max_views; q += blockDim.x) {
+        const int p = q / G.max_views, k = q % G.max_views;
+        const int i = s_pi[p], j = s_pj[p];
+        const int nvb = G.block_nviews[i];
+        int c = -1;
+        if (k < nvb && A.cells_mode != BSGD_CELLS_NONE) {
+            if (replay) {
+                c = rep[1 + 2 * np + p * G.max_views + k];
+            } else {
+                const double u = draw_u(A.seed, it, kLaneCells + p * nvb + k);
+                if (A.cells_mode == BSGD_CELLS_UNIFORM) {
+                    c = min((int)(u * A.n_cells), A.n_cells - 1);
+                } else {
+                    const int a = G.block_views[i * G.max_views + k];
+                    c = pick_weighted(u, A.cw + ((size_t)j * G.n_views + a) * A.n_cells, A.n_cells, 1);
+                }
+            }
+        }
+        A.cells[p * G.max_views + k] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        Work &W = *A.work;
+        W.n_pairs = np;
+        int nc = 0, nr = 0;
+        for (int p = 0; p < np; ++p) {
+            W.pair_i[p] = s_pi[p];
+            W.pair_j[p] = s_pj[p];
+            bool seen = false;
+            for (int t = 0; t < nc; ++t) seen |= W.cols[t] == s_pj[p];
+            if (!seen) W.cols[nc++] = s_pj[p];
+            seen = false;
+            for (int t = 0; t < nr; ++t) seen |= W.rows[t] == s_pi[p];
+            if (!seen) W.rows[nr++] = s_pi[p];
+        }
+        W.n_cols = nc;
+        W.n_rows = nr;
+        // voxel-ray updates of this iteration (FP + BP)
+        unsigned long long upd = 0;
+        for (int p = 0; p < np; ++p) {
+            const int i = s_pi[p], j = s_pj[p];
+            for (int k = 0; k < G.block_nviews[i]; ++k) {
+                const int a = G.block_views[i * G.max_views + k];
+                const unsigned long long *cn = A.counts + ((size_t)j * G.n_views + a) * A.n_cells;
+                const int c = A.cells[p * G.max_views + k];
+                if (c >= 0) upd += cn[c];
+                else for (int s = 0; s < A.n_cells; ++s) upd += cn[s];
+            }
+        }
+        *A.updates += 2ull * upd;
+        if (A.trace && it < A.trace_cap) {
+            int32_t *t = A.trace + it * A.stride;
+            t[0] = np;
+            for (int p = 0; p < np; ++p) {
+                t[1 + 2 * p] = s_pi[p];
+                t[2 + 2 * p] = s_pj[p];
+            }
+        }
+    }
+    if (A.trace && it < A.trace_cap) {
+        int32_t *t = A.trace + it * A.stride;
+        for (int q = tid; q < np * G.max_views; q += blockDim.x) t[1 + 2 * np + q] = A.cells[q];
+        for (int q = 1 + 2 * np + np * G.max_views + tid; q < A.stride; q += blockDim.x) t[q] = -1;
+    }
+    __syncthreads();
+    if (tid == 0) *A.iter = it + 1;
+}
+
+// r = y - sum_j z^j over every row of the selected row blocks (used when
+// several column blocks of one row block are selected, so the FPs cannot
+// update r themselves), with the FP64 row-block residual sums.
+template <typename T>
+__global__ void residual_kernel(const DeviceGeom G, const SolveDev S) {
+    const Work &W = *S.work;
+    const int rb = blockIdx.z;
+    if (rb >= W.n_rows) return;
+    const int i = W.rows[rb];
+    const int slot = blockIdx.y;
+    if (slot >= G.block_nviews[i]) return;
+    const int a = G.block_views[i * G.max_views + slot];
+    const int per = G.nv * G.nu;
+    const T *y = reinterpret_cast<const T *>(S.y);
+    const T *z = reinterpret_cast<const T *>(S.z);
+    T *r = reinterpret_cast<T *>(S.r);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < per; k += gridDim.x * blockDim.x) {
+        const int64_t row = (int64_t)a * per + k;
+        float zs = 0.f;
+        for (int jj = 0; jj < G.N; ++jj) zs += ldv(z + (int64_t)jj * G.n_rows + row);
+        const float rn = rnd(ldf(y + row) - zs, r);
+        const float ro = ldv(r + row);
+        if (rn != ro) {
+            stf(r + row, rn);
+            atomicAdd(S.S + (size_t)i * G.nv + k / G.nu, (double)rn * rn - (double)ro * ro);
+        }
+    }
+}
+
+// x_J += mu g_J for the selected column blocks. With 16-bit storage the
+// state keeps a low-order term xlo of the same type (compensated storage): the
+// update works on x + xlo in FP32 and splits the result back, so steps smaller
+// than half an ulp of x still accumulate instead of being rounded away.
+template <typename T>
+__global__ void update_kernel(const DeviceGeom G, const SolveDev S, T *__restrict__ x,
+                              T *__restrict__ xlo) {
+    const Work &W = *S.work;
+    const int c = blockIdx.y;
+    if (c >= W.n_cols) return;
+    const int j = W.cols[c];
+    const int64_t b0 = (int64_t)G.plane_start[j] * G.plane_stride;
+    const int64_t b1 = (int64_t)G.plane_start[j + 1] * G.plane_stride;
+    const float mu = (float)*S.mu;
+    for (int64_t k = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b1;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        if (xlo == nullptr) {
+            stf(x + k, fmaf(mu, S.g[k], ldv(x + k)));
+        } else {
+            const float s = fmaf(mu, S.g[k], ldv(x + k) + ldv(xlo + k));
+            const float hi = rnd(s, x);
+            stf(x + k, hi);
+            stf(xlo + k, s - hi);
+        }
+    }
+}
+
+// S[block(a)][v] += r^2 over all rows (the FP64 residual table from scratch).
+template <typename T>
+__global__ void norm_table_kernel(const DeviceGeom G, const T *__restrict__ r, double *S) {
+    const int64_t per_row = G.nu;
+    const int64_t n_lines = (int64_t)G.n_views * G.nv;
+    for (int64_t line = blockIdx.x; line < n_lines; line += gridDim.x) {
+        const int a = (int)(line / G.nv), v = (int)(line % G.nv);
+        double acc = 0.0;
+        for (int64_t u = threadIdx.x; u < per_row; u += blockDim.x) {
+            const float x = ldv(r + line * per_row + u);
+            acc += (double)x * x;
+        }
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0 && acc != 0.0)
+            atomicAdd(S + (size_t)G.view_block[a] * G.nv + v, acc);
+    }
+}
+
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI *__restrict__ in, TO *__restrict__ out, int64_t n) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        stf(out + k, ldf(in + k));
+}
+
+// Per (view, cell) sums of an FP of block J's indicator (FP64), then the floor.
+__global__ void cell_sum_kernel(const DeviceGeom G, const float *__restrict__ yj, int j,
+                                int n_cells, double *cw) {
+    const int64_t n = G.n_rows;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const float val = yj[row];
+        if (val == 0.f) continue;
+        const int u = (int)(row % G.nu), v = (int)((row / G.nu) % G.nv);
+        const int a = (int)(row / ((int64_t)G.nu * G.nv));
+        int c = 0;
+        if (n_cells == 2) c = u >= G.nu / 2;
+        if (n_cells == 4) c = (v >= G.nv / 2) * 2 + (u >= G.nu / 2);
+        atomicAdd(cw + ((size_t)j * G.n_views + a) * n_cells + c, (double)val);
+    }
+}
+
+__global__ void cell_floor_kernel(const DeviceGeom G, int n_cells, double *cw) {
+    const int64_t n = (int64_t)G.N * G.n_views;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        double *w = cw + k * n_cells;
+        double tot = 0.0;
+        for (int s = 0; s < n_cells; ++s) tot += w[s];
+        for (int s = 0; s < n_cells; ++s) w[s] = fmax(w[s], kCellFloor * tot);
+    }
+}
+
+// ---- power iteration helpers (FP64 vector state) --------------------------
+
+__global__ void sumsq_kernel(const float *__restrict__ a, int64_t b0, int64_t b1, double *out) {
+    double acc = 0.0;
+    for (int64_t k = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b1;
+         k += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)a[k] * a[k];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ double part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) atomicAdd(out, acc);
+    }
+}
+
+// v = w / ||w|| (FP64) on [b0, b1); v32 = float(v); zero w.
+__global__ void normalize_kernel(float *__restrict__ w, double *__restrict__ v64,
+                                 float *__restrict__ v32, int64_t b0, int64_t b1,
+                                 const double *nrm2, int init) {
+    const double inv = init ? 1.0 / sqrt((double)(b1 - b0)) : 1.0 / sqrt(*nrm2);
+    for (int64_t k = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b1;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double v = init ? inv : (double)w[k] * inv;
+        v64[k - b0] = v;
+        v32[k] = (float)v;
+        w[k] = 0.f;
+    }
+}
+
+int grid_for(int64_t n, int threads = 256) {
+    int64_t b = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+}  // namespace bsgd
+
+using namespace bsgd;
+
+// ---------------------------------------------------------------------------
+// State
+
+struct bsgd_state {
+    const bsgd_geometry *g = nullptr;
+    bsgd_solve_params p{};
+    int kM = 1, kN = 1, P = 1, epoch_len = 1;
+    bsgd_dtype st = BSGD_F32;
+    bool fused = true;
+    int max_tiles = 0;
+    int n_cells = 1;
+    int stride = 0;
+    int64_t trace_cap = 0;
+    int64_t iters = 0;          // iterations launched
+    double mu = 0.0;
+    // device memory
+    void *y = nullptr, *z = nullptr, *rt = nullptr, *r = nullptr;
+    void *xlo = nullptr;        // low-order image term (16-bit storage only)
+    float *grad = nullptr;
+    double *S = nullptr, *cw = nullptr, *d_mu = nullptr;
+    Work *work = nullptr;
+    int *cells = nullptr, *wband = nullptr;
+    int64_t *d_iter = nullptr;
+    int32_t *trace = nullptr, *replay = nullptr;
+    int64_t replay_start = 0, replay_n = 0;
+    unsigned long long *counts = nullptr, *updates = nullptr;
+    SolveDev dev{};
+    // tracing: event pairs per stage (a pool reused after each read)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    int64_t launches[BSGD_N_STAGES] = {};
+    double ms[BSGD_N_STAGES] = {};
+};
+
+static cudaEvent_t next_event(bsgd_state *s) {
+    if (s->ev_used == s->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        s->ev_pool.push_back(e);
+    }
+    return s->ev_pool[s->ev_used++];
+}
+
+// Record the start of a stage; returns its begin event (or null when off).
+static cudaEvent_t stage_begin(bsgd_state *s, cudaStream_t st) {
+    if (!s->profiling) return nullptr;
+    cudaEvent_t b = next_event(s);
+    if (b) cudaEventRecord(b, st);
+    return b;
+}
+
+static void stage_end(bsgd_state *s, int stage, cudaEvent_t b, int launches, cudaStream_t st) {
+    if (!s->profiling || !b) return;
+    cudaEvent_t e = next_event(s);
+    if (!e) return;
+    cudaEventRecord(e, st);
+    s->marks.push_back({stage, {b, e}});
+    s->launches[stage] += launches;
+}
+
+static void free_state(bsgd_state *s) {
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->grad, s->S, s->cw, s->d_mu, s->work, s->cells,
+                    s->wband, s->d_iter, s->trace, s->replay, s->counts, s->updates};
+    for (void *p : ptrs) cudaFree(p);
+    delete s;
+}
+
+static bsgd_status dalloc(void **p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? BSGD_ERR_OOM : BSGD_ERR_CUDA,
+                    std::string("cudaMalloc of ") + std::to_string(bytes) +
+                        " bytes: " + cudaGetErrorString(e));
+    }
+    return BSGD_OK;
+}
+
+namespace bsgd {
+
+bsgd_status convert(const void *in, bsgd_dtype it, void *out, bsgd_dtype ot, int64_t n,
+                    cudaStream_t st) {
+    if (it == ot) {
+        BSGD_CUDA(cudaMemcpyAsync(out, in, n * dtype_size(it), cudaMemcpyDeviceToDevice, st));
+        return BSGD_OK;
+    }
+    const int gb = grid_for(n);
+#define CV(TI, TO) convert_kernel<TI, TO><<<gb, 256, 0, st>>>((const TI *)in, (TO *)out, n)
+    if (it == BSGD_F32 && ot == BSGD_BF16) CV(float, __nv_bfloat16);
+    else if (it == BSGD_F32 && ot == BSGD_F16) CV(float, __half);
+    else if (it == BSGD_BF16 && ot == BSGD_F32) CV(__nv_bfloat16, float);
+    else if (it == BSGD_BF16 && ot == BSGD_F16) CV(__nv_bfloat16, __half);
+    else if (it == BSGD_F16 && ot == BSGD_F32) CV(__half, float);
+    else CV(__half, __nv_bfloat16);
+#undef CV
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+bsgd_status norm_table(const bsgd_geometry *g, const void *r, bsgd_dtype t, double *S,
+                       cudaStream_t st) {
+    BSGD_CUDA(cudaMemsetAsync(S, 0, sizeof(double) * g->M * g->desc.nv, st));
+    const int64_t lines = (int64_t)g->desc.n_views * g->desc.nv;
+    const int gb = (int)std::min<int64_t>(lines, 152 * 32);
+    if (t == BSGD_F32) norm_table_kernel<float><<<gb, 128, 0, st>>>(g->dg, (const float *)r, S);
+    else if (t == BSGD_BF16) norm_table_kernel<__nv_bfloat16><<<gb, 128, 0, st>>>(g->dg, (const __nv_bfloat16 *)r, S);
+    else norm_table_kernel<__half><<<gb, 128, 0, st>>>(g->dg, (const __half *)r, S);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+// lambda ~ ||A_rows^J||^2 by power iteration (see bsgd.h).
+bsgd_status power_iteration(const bsgd_geometry *g, int j, int iters, const int *row_ids, int n_rb,
+                            double *lambda, cudaStream_t st) {
+    const int64_t b0 = (int64_t)g->plane_start[j] * g->dg.plane_stride;
+    const int64_t b1 = (int64_t)g->plane_start[j + 1] * g->dg.plane_stride;
+    const int64_t n = g->n_cols(), m = g->n_rows();
+    float *v32 = nullptr, *w = nullptr, *y = nullptr;
+    double *v64 = nullptr, *nrm = nullptr;
+    bsgd_status s = BSGD_OK;
+    auto cleanup = [&]() {
+        cudaFree(v32); cudaFree(w); cudaFree(y); cudaFree(v64); cudaFree(nrm);
+    };
+    if ((s = dalloc((void **)&v32, n * 4)) || (s = dalloc((void **)&w, n * 4)) ||
+        (s = dalloc((void **)&y, m * 4)) || (s = dalloc((void **)&v64, (b1 - b0) * 8)) ||
+        (s = dalloc((void **)&nrm, 8 * (iters + 2)))) {
+        cleanup();
+        return s;
+    }
+    std::vector<int> all;
+    if (!row_ids) {
+        for (int i = 0; i < g->M; ++i) all.push_back(i);
+        row_ids = all.data();
+        n_rb = g->M;
+    }
+    PlainLaunch L{row_ids, n_rb, j, j + 1, 0};
+    const int gb = grid_for(b1 - b0);
+    auto run = [&]() -> bsgd_status {
+        BSGD_CUDA(cudaMemsetAsync(v32, 0, n * 4, st));
+        BSGD_CUDA(cudaMemsetAsync(w, 0, n * 4, st));
+        BSGD_CUDA(cudaMemsetAsync(nrm, 0, 8 * (iters + 2), st));
+        normalize_kernel<<<gb, 256, 0, st>>>(w, v64, v32, b0, b1, nrm, 1);
+        for (int k = 0; k < iters; ++k) {
+            BSGD_CUDA(cudaMemsetAsync(y, 0, m * 4, st));
+            BSGD_TRY(launch_fp_plain(g, L, v32, BSGD_F32, y, BSGD_F32, 1, st));
+            BSGD_TRY(launch_bp_plain(g, L, y, BSGD_F32, w, 1.0f, st));
+            sumsq_kernel<<<gb, 256, 0, st>>>(w, b0, b1, nrm + k);
+            normalize_kernel<<<gb, 256, 0, st>>>(w, v64, v32, b0, b1, nrm + k, 0);
+        }
+        BSGD_CUDA(cudaMemsetAsync(y, 0, m * 4, st));
+        BSGD_TRY(launch_fp_plain(g, L, v32, BSGD_F32, y, BSGD_F32, 1, st));
+        sumsq_kernel<<<grid_for(m), 256, 0, st>>>(y, 0, m, nrm + iters);
+        BSGD_CUDA(cudaGetLastError());
+        BSGD_CUDA(cudaMemcpyAsync(lambda, nrm + iters, 8, cudaMemcpyDeviceToHost, st));
+        BSGD_CUDA(cudaStreamSynchronize(st));
+        return BSGD_OK;
+    };
+    s = run();
+    cleanup();
+    return s;
+}
+
+}  // namespace bsgd
+
+extern "C" bsgd_status bsgd_power_iteration(const bsgd_geometry *g, int col_block, int iters,
+                                            const int32_t *row_blocks, int n_rb,
+                                            double *lambda_out, void *stream) {
+    if (!g || !lambda_out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (col_block < 0 || col_block >= g->N) return fail(BSGD_ERR_INVALID_ARG, "col_block out of range");
+    if (iters < 0) return fail(BSGD_ERR_INVALID_ARG, "iters < 0");
+    if (row_blocks)
+        for (int k = 0; k < n_rb; ++k)
+            if (row_blocks[k] < 0 || row_blocks[k] >= g->M)
+                return fail(BSGD_ERR_INVALID_ARG, "row block id out of range");
+    return power_iteration(g, col_block, iters, (const int *)row_blocks, row_blocks ? n_rb : 0,
+                           lambda_out, (cudaStream_t)stream);
+}
+
+static bsgd_status check_params(const bsgd_geometry *g, const bsgd_solve_params *p) {
+    if (!(p->alpha > 0 && p->alpha <= 1) || !(p->gamma > 0 && p->gamma <= 1))
+        return fail(BSGD_ERR_INVALID_ARG, "alpha and gamma must lie in (0, 1]");
+    if (!dtype_ok(p->storage)) return fail(BSGD_ERR_INVALID_ARG, "bad storage dtype");
+    if (p->step_rule < BSGD_STEP_STRIP || p->step_rule > BSGD_STEP_FIXED)
+        return fail(BSGD_ERR_INVALID_ARG, "bad step rule");
+    if (p->step_rule == BSGD_STEP_FIXED && !(p->mu > 0))
+        return fail(BSGD_ERR_INVALID_ARG, "fixed step needs mu > 0");
+    if (p->step_rule != BSGD_STEP_FIXED && (!(p->rho > 0) || p->power_iters < 1))
+        return fail(BSGD_ERR_INVALID_ARG, "STRIP / BLOCK steps need rho > 0 and power_iters >= 1");
+    if (p->pair_sampling != BSGD_PAIRS_UNIFORM && p->pair_sampling != BSGD_PAIRS_RESIDUAL)
+        return fail(BSGD_ERR_INVALID_ARG, "bad pair sampling");
+    if (p->cells < BSGD_CELLS_NONE || p->cells > BSGD_CELLS_UNIFORM)
+        return fail(BSGD_ERR_INVALID_ARG, "bad cell sampling");
+    if (p->cells != BSGD_CELLS_NONE && p->n_cells != (g->desc.nv > 1 ? 4 : 2))
+        return fail(BSGD_ERR_INVALID_ARG, "n_cells must be 4 (3D) or 2 (2D)");
+    if (g->M > kMaxSampleBlocks || g->N > kMaxSampleBlocks || g->M > 64)
+        return fail(BSGD_ERR_INVALID_ARG, "the solver supports M <= 64 and N <= 1024");
+    if (p->pair_sampling == BSGD_PAIRS_RESIDUAL && g->M * g->N > kMaxPairs * 64)
+        return fail(BSGD_ERR_INVALID_ARG, "residual sampling supports M * N <= 4096");
+    if (p->tv_lambda < 0 || (p->tv_lambda > 0 && p->tv_iters < 1))
+        return fail(BSGD_ERR_INVALID_ARG, "tv_lambda >= 0 and tv_iters >= 1");
+    return BSGD_OK;
+}
+
+namespace bsgd {
+bsgd_status tv_prox_impl(const bsgd_geometry *g, void *x, bsgd_dtype xt, double kappa, int iters,
+                         cudaStream_t st, void *xlo);
+}
+
+extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solve_params *p,
+                                         const void *y, bsgd_dtype yt, void *stream,
+                                         bsgd_state **out) {
+    if (!g || !p || !y || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (!dtype_ok(yt)) return fail(BSGD_ERR_INVALID_ARG, "bad y dtype");
+    BSGD_TRY(check_params(g, p));
+    cudaStream_t st = (cudaStream_t)stream;
+    bsgd_state *s = new (std::nothrow) bsgd_state();
+    if (!s) return fail(BSGD_ERR_OOM, "host allocation failed");
+    s->g = g;
+    s->p = *p;
+    s->kM = std::max(1, (int)std::lround(p->alpha * g->M));
+    s->kN = std::max(1, (int)std::lround(p->gamma * g->N));
+    s->P = s->kM * s->kN;
+    s->epoch_len = std::max(1, (int)std::lround(1.0 / (p->alpha * p->gamma)));
+    s->st = (bsgd_dtype)p->storage;
+    s->fused = s->kN == 1;
+    s->n_cells = p->cells == BSGD_CELLS_NONE ? 1 : p->n_cells;
+    if (s->P > kMaxPairs) {
+        free_state(s);
+        return fail(BSGD_ERR_INVALID_ARG, "more than 64 pairs per iteration");
+    }
+    if (p->pair_sampling == BSGD_PAIRS_RESIDUAL && s->P != 1) {
+        free_state(s);
+        return fail(BSGD_ERR_INVALID_ARG, "residual pair sampling draws one pair per iteration");
+    }
+    s->stride = 1 + 2 * s->P + s->P * g->max_views;
+    s->trace_cap = 65536;
+    const int64_t R = g->n_rows(), C = g->n_cols();
+    const size_t es = dtype_size(s->st);
+    const int N = g->N, M = g->M, V = g->desc.n_views;
+    bsgd_status e = BSGD_OK;
+    if ((e = dalloc(&s->y, R * es)) || (e = dalloc(&s->z, (size_t)N * R * es)) ||
+        (e = dalloc(&s->rt, (size_t)N * R * es)) || (e = dalloc(&s->r, R * es)) ||
+        (e = dalloc((void **)&s->grad, C * 4)) || (e = dalloc((void **)&s->S, 8 * (size_t)M * g->desc.nv)) ||
+        (e = dalloc((void **)&s->d_mu, 8)) || (e = dalloc((void **)&s->work, sizeof(Work))) ||
+        (e = dalloc((void **)&s->cells, 4 * (size_t)kMaxPairs * g->max_views)) ||
+        (e = dalloc((void **)&s->wband, 4 * g->wband.size())) ||
+        (e = dalloc((void **)&s->d_iter, 8)) ||
+        (e = dalloc((void **)&s->trace, 4 * (size_t)s->trace_cap * s->stride)) ||
+        (e = dalloc((void **)&s->counts, 8 * (size_t)N * V * s->n_cells)) ||
+        (e = dalloc((void **)&s->updates, 8)) ||
+        (s->st != BSGD_F32 && (e = dalloc(&s->xlo, C * es))) ||
+        (p->cells == BSGD_CELLS_GEOMETRIC && (e = dalloc((void **)&s->cw, 8 * (size_t)N * V * s->n_cells)))) {
+        free_state(s);
+        return e;
+    }
+    auto init = [&]() -> bsgd_status {
+        BSGD_TRY(convert(y, yt, s->y, s->st, R, st));
+        BSGD_CUDA(cudaMemcpyAsync(s->r, s->y, R * es, cudaMemcpyDeviceToDevice, st));
+        BSGD_CUDA(cudaMemsetAsync(s->z, 0, (size_t)N * R * es, st));
+        BSGD_CUDA(cudaMemsetAsync(s->rt, 0, (size_t)N * R * es, st));
+        BSGD_CUDA(cudaMemsetAsync(s->grad, 0, C * 4, st));
+        if (s->xlo) BSGD_CUDA(cudaMemsetAsync(s->xlo, 0, C * es, st));
+        BSGD_CUDA(cudaMemsetAsync(s->d_iter, 0, 8, st));
+        BSGD_CUDA(cudaMemsetAsync(s->updates, 0, 8, st));
+        BSGD_CUDA(cudaMemsetAsync(s->counts, 0, 8 * (size_t)N * V * s->n_cells, st));
+        BSGD_CUDA(cudaMemsetAsync(s->work, 0, sizeof(Work), st));
+        BSGD_CUDA(cudaMemsetAsync(s->cells, 0xff, 4 * (size_t)kMaxPairs * g->max_views, st));
+        BSGD_CUDA(cudaMemcpyAsync(s->wband, g->wband.data(), 4 * g->wband.size(),
+                                  cudaMemcpyHostToDevice, st));
+        BSGD_TRY(norm_table(g, s->r, s->st, s->S, st));
+        for (int j = 0; j < N; ++j)
+            BSGD_TRY(launch_count_cells(g, j, s->n_cells, s->counts + (size_t)j * V * s->n_cells, st));
+        if (p->cells == BSGD_CELLS_GEOMETRIC) {
+            // w(a, c, J) = 1^T A_{(a,c)}^J 1: FP of J's indicator, summed per cell
+            float *ind = nullptr, *yj = nullptr;
+            BSGD_TRY(dalloc((void **)&ind, C * 4));
+            bsgd_status e2 = dalloc((void **)&yj, R * 4);
+            if (e2) { cudaFree(ind); return e2; }
+            BSGD_CUDA(cudaMemsetAsync(s->cw, 0, 8 * (size_t)N * V * s->n_cells, st));
+            std::vector<int> all(M);
+            for (int i = 0; i < M; ++i) all[i] = i;
+            std::vector<float> ones;
+            for (int j = 0; j < N && !e2; ++j) {
+                cudaMemsetAsync(ind, 0, C * 4, st);
+                const int64_t b0 = (int64_t)g->plane_start[j] * g->dg.plane_stride;
+                ones.assign(g->block_cols(j), 1.0f);
+                cudaMemcpyAsync(ind + b0, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice, st);
+                cudaStreamSynchronize(st);
+                cudaMemsetAsync(yj, 0, R * 4, st);
+                PlainLaunch L{all.data(), M, j, j + 1, 0};
+                e2 = launch_fp_plain(g, L, ind, BSGD_F32, yj, BSGD_F32, 1, st);
+                if (!e2) cell_sum_kernel<<<grid_for(R), 256, 0, st>>>(g->dg, yj, j, s->n_cells, s->cw);
+            }
+            if (!e2) cell_floor_kernel<<<grid_for((int64_t)N * V), 256, 0, st>>>(g->dg, s->n_cells, s->cw);
+            cudaStreamSynchronize(st);
+            cudaFree(ind);
+            cudaFree(yj);
+            if (e2) return e2;
+            BSGD_CUDA(cudaGetLastError());
+        }
+        // step size
+        if (p->step_rule == BSGD_STEP_FIXED) {
+            s->mu = p->mu;
+        } else {
+            double lmax = 0.0;
+            for (int j = 0; j < N; ++j) {
+                if (p->step_rule == BSGD_STEP_STRIP) {
+                    double lam = 0.0;
+                    BSGD_TRY(power_iteration(g, j, p->power_iters, nullptr, 0, &lam, st));
+                    lmax = std::max(lmax, lam);
+                } else {
+                    for (int i = 0; i < M; ++i) {
+                        double lam = 0.0;
+                        BSGD_TRY(power_iteration(g, j, p->power_iters, &i, 1, &lam, st));
+                        lmax = std::max(lmax, lam);
+                    }
+                }
+            }
+            if (!(lmax > 0)) return fail(BSGD_ERR_INVALID_ARG, "A^J is zero for every block");
+            s->mu = p->rho / lmax;
+        }
+        BSGD_CUDA(cudaMemcpyAsync(s->d_mu, &s->mu, 8, cudaMemcpyHostToDevice, st));
+        BSGD_CUDA(cudaStreamSynchronize(st));
+        return BSGD_OK;
+    };
+    if ((e = init())) {
+        cudaStreamSynchronize(st);
+        free_state(s);
+        return e;
+    }
+    std::vector<int> all(V);
+    for (int a = 0; a < V; ++a) all[a] = a;
+    for (int j = 0; j < N; ++j)
+        s->max_tiles = std::max(s->max_tiles, tiles_for(g, all, j, j + 1, tile_u(g), tile_v(g)));
+    SolveDev &d = s->dev;
+    d.y = s->y;
+    d.z = s->z;
+    d.rt = s->rt;
+    d.r = s->r;
+    d.g = s->grad;
+    d.S = s->S;
+    d.work = s->work;
+    d.cells = s->cells;
+    d.n_cells = s->n_cells;
+    d.mu = s->d_mu;
+    *out = s;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_state_destroy(bsgd_state *s) {
+    if (!s) return fail(BSGD_ERR_INVALID_ARG, "state is NULL");
+    cudaDeviceSynchronize();
+    free_state(s);
+    return BSGD_OK;
+}
+
+static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
+    const bsgd_geometry *g = s->g;
+    SampleArgs A{};
+    A.G = g->dg;
+    A.work = s->work;
+    A.cells = s->cells;
+    A.iter = s->d_iter;
+    A.seed = s->p.seed;
+    A.pairs_mode = s->p.pair_sampling;
+    A.cells_mode = s->p.cells;
+    A.n_cells = s->n_cells;
+    A.kM = s->kM;
+    A.kN = s->kN;
+    A.S = s->S;
+    A.wband = s->wband;
+    A.cw = s->cw;
+    A.replay = s->replay;
+    A.replay_start = s->replay_start;
+    A.replay_n = s->replay_n;
+    A.trace = s->trace;
+    A.trace_cap = s->trace_cap;
+    A.stride = s->stride;
+    A.counts = s->counts;
+    A.updates = s->updates;
+    cudaEvent_t b = stage_begin(s, st);
+    sample_kernel<<<1, kSampleThreads, 0, st>>>(A);
+    BSGD_CUDA(cudaGetLastError());
+    stage_end(s, BSGD_STAGE_SAMPLE, b, 1, st);
+    if (s->max_tiles > 0) {
+        b = stage_begin(s, st);
+        BSGD_TRY(launch_fp_solve(g, s->dev, x, s->st, s->P, s->max_tiles, s->fused, st));
+        stage_end(s, BSGD_STAGE_FP, b, 1, st);
+        if (!s->fused) {
+            b = stage_begin(s, st);
+            dim3 grid(std::max(1, std::min(64, (g->desc.nu * g->desc.nv + 255) / 256)), g->max_views, s->kM);
+            if (s->st == BSGD_F32) residual_kernel<float><<<grid, 256, 0, st>>>(g->dg, s->dev);
+            else if (s->st == BSGD_BF16) residual_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(g->dg, s->dev);
+            else residual_kernel<__half><<<grid, 256, 0, st>>>(g->dg, s->dev);
+            BSGD_CUDA(cudaGetLastError());
+            stage_end(s, BSGD_STAGE_RESIDUAL, b, 1, st);
+        }
+        b = stage_begin(s, st);
+        BSGD_TRY(launch_bp_solve(g, s->dev, s->st, s->P, s->max_tiles, st));
+        stage_end(s, BSGD_STAGE_BP, b, 1, st);
+    }
+    int64_t maxJ = 0;
+    for (int j = 0; j < g->N; ++j) maxJ = std::max(maxJ, g->block_cols(j));
+    dim3 ug(std::max(1, std::min<int>((int)((maxJ + 255) / 256), 152 * 8)), s->kN);
+    b = stage_begin(s, st);
+    if (s->st == BSGD_F32) update_kernel<float><<<ug, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr);
+    else if (s->st == BSGD_BF16) update_kernel<__nv_bfloat16><<<ug, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo);
+    else update_kernel<__half><<<ug, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo);
+    BSGD_CUDA(cudaGetLastError());
+    stage_end(s, BSGD_STAGE_UPDATE, b, 1, st);
+    s->iters += 1;
+    if (s->p.tv_lambda > 0 && s->iters % s->epoch_len == 0) {
+        b = stage_begin(s, st);
+        BSGD_TRY(tv_prox_impl(g, x, s->st, s->mu * s->p.tv_lambda, s->p.tv_iters, st, s->xlo));
+        stage_end(s, BSGD_STAGE_TV, b, 2 * s->p.tv_iters + 2, st);
+    }
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void *stream) {
+    if (!s || !x) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (n_iters < 0) return fail(BSGD_ERR_INVALID_ARG, "n_iters < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < n_iters; ++k) BSGD_TRY(one_iteration(s, x, st));
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_state_query(bsgd_state *s, bsgd_report *out, void *stream) {
+    if (!s || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = s->g->M * s->g->desc.nv;
+    std::vector<double> S(n);
+    unsigned long long upd = 0;
+    BSGD_CUDA(cudaMemcpyAsync(S.data(), s->S, 8 * n, cudaMemcpyDeviceToHost, st));
+    BSGD_CUDA(cudaMemcpyAsync(&upd, s->updates, 8, cudaMemcpyDeviceToHost, st));
+    BSGD_CUDA(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (double v : S) tot += v;
+    out->residual_norm = std::sqrt(std::max(tot, 0.0));
+    out->mu = s->mu;
+    out->iteration = s->iters;
+    out->epoch = (double)s->iters / s->epoch_len;
+    out->updates = (int64_t)upd;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_state_profile(bsgd_state *s, int enable) {
+    if (!s) return fail(BSGD_ERR_INVALID_ARG, "state is NULL");
+    s->profiling = enable != 0;
+    s->marks.clear();
+    s->ev_used = 0;
+    for (int k = 0; k < BSGD_N_STAGES; ++k) {
+        s->launches[k] = 0;
+        s->ms[k] = 0.0;
+    }
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_state_read_profile(bsgd_state *s, bsgd_profile *out, void *stream) {
+    if (!s || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    BSGD_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    for (auto &m : s->marks) {
+        float t = 0.f;
+        BSGD_CUDA(cudaEventElapsedTime(&t, m.second.first, m.second.second));
+        s->ms[m.first] += t;
+    }
+    s->marks.clear();
+    s->ev_used = 0;
+    for (int k = 0; k < BSGD_N_STAGES; ++k) {
+        out->launches[k] = s->launches[k];
+        out->ms[k] = s->ms[k];
+    }
+    return BSGD_OK;
+}
+
+extern "C" int64_t bsgd_trace_stride(const bsgd_state *s) { return s ? s->stride : 0; }
+
+extern "C" bsgd_status bsgd_state_read_trace(bsgd_state *s, int32_t *host, int64_t cap,
+                                             int64_t n_iters, void *stream) {
+    if (!s || !host) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (n_iters < 0 || n_iters > s->iters || n_iters > s->trace_cap)
+        return fail(BSGD_ERR_INVALID_ARG, "n_iters beyond the recorded iterations");
+    if (n_iters * s->stride > cap) return fail(BSGD_ERR_INVALID_ARG, "host buffer too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    BSGD_CUDA(cudaMemcpyAsync(host, s->trace, 4 * n_iters * s->stride, cudaMemcpyDeviceToHost, st));
+    BSGD_CUDA(cudaStreamSynchronize(st));
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_state_set_replay(bsgd_state *s, const int32_t *host, int64_t n_iters) {
+    if (!s || (!host && n_iters > 0)) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (n_iters < 0) return fail(BSGD_ERR_INVALID_ARG, "n_iters < 0");
+    const bsgd_geometry *g = s->g;
+    for (int64_t t = 0; t < n_iters; ++t) {
+        const int32_t *e = host + t * s->stride;
+        if (e[0] < 1 || e[0] > s->P) return fail(BSGD_ERR_INVALID_ARG, "bad pair count in trace");
+        for (int p = 0; p < e[0]; ++p) {
+            if (e[1 + 2 * p] < 0 || e[1 + 2 * p] >= g->M || e[2 + 2 * p] < 0 || e[2 + 2 * p] >= g->N)
+                return fail(BSGD_ERR_INVALID_ARG, "block id out of range in trace");
+            for (int k = 0; k < g->max_views; ++k) {
+                const int c = e[1 + 2 * e[0] + p * g->max_views + k];
+                if (c < -1 || c >= s->n_cells || (c == -1 && s->p.cells != BSGD_CELLS_NONE &&
+                                                  k < (int)g->block_views[e[1 + 2 * p]].size()))
+                    return fail(BSGD_ERR_INVALID_ARG, "bad cell id in trace");
+            }
+        }
+    }
+    cudaDeviceSynchronize();
+    cudaFree(s->replay);
+    s->replay = nullptr;
+    s->replay_n = 0;
+    if (n_iters > 0) BSGD_TRY(upload((void **)&s->replay, host, 4 * n_iters * s->stride));
+    s->replay_start = s->iters;
+    s->replay_n = n_iters;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_params *p,
+                                  const void *y, bsgd_dtype yt, void *x, bsgd_dtype xt,
+                                  bsgd_report *out, void *stream) {
+    if (!g || !p || !y || !x) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (!dtype_ok(yt) || !dtype_ok(xt)) return fail(BSGD_ERR_INVALID_ARG, "bad dtype");
+    cudaStream_t st = (cudaStream_t)stream;
+    auto on_host = [](const void *ptr) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return true;
+        }
+        return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+    };
+    const int64_t R = g->n_rows(), C = g->n_cols();
+    const bool yh = on_host(y), xh = on_host(x);
+    void *dy = nullptr, *dx = nullptr, *xs = nullptr;
+    bsgd_state *s = nullptr;
+    bsgd_status e = BSGD_OK;
+    auto body = [&]() -> bsgd_status {
+        const void *yy = y;
+        if (yh) {
+            BSGD_TRY(dalloc(&dy, R * dtype_size(yt)));
+            BSGD_CUDA(cudaMemcpyAsync(dy, y, R * dtype_size(yt), cudaMemcpyHostToDevice, st));
+            yy = dy;
+        }
+        BSGD_TRY(bsgd_state_create(g, p, yy, yt, stream, &s));
+        const bsgd_dtype sd = (bsgd_dtype)p->storage;
+        BSGD_TRY(dalloc(&xs, C * dtype_size(sd)));
+        BSGD_CUDA(cudaMemsetAsync(xs, 0, C * dtype_size(sd), st));
+        BSGD_TRY(bsgd_block_step(s, xs, p->epochs * s->epoch_len, stream));
+        void *xo = x;
+        if (xh) {
+            BSGD_TRY(dalloc(&dx, C * dtype_size(xt)));
+            xo = dx;
+        }
+        BSGD_TRY(convert(xs, sd, xo, xt, C, st));
+        if (xh) BSGD_CUDA(cudaMemcpyAsync(x, dx, C * dtype_size(xt), cudaMemcpyDeviceToHost, st));
+        if (out) BSGD_TRY(bsgd_state_query(s, out, stream));
+        BSGD_CUDA(cudaStreamSynchronize(st));
+        return BSGD_OK;
+    };
+    e = body();
+    cudaStreamSynchronize(st);
+    if (s) bsgd_state_destroy(s);
+    cudaFree(dy);
+    cudaFree(dx);
+    cudaFree(xs);
+    return e;
+}

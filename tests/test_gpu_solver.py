@@ -1,0 +1,225 @@
+"""GPU parity of the BSGD iteration against the FP64 oracle, through the C ABI.
+
+Uniform sampling draws the same blocks on both sides (the SplitMix64 spec is
+implemented independently on each), so whole trajectories are compared. Where
+a floating-point weight decides the draw (residual pairs, geometric cells), the
+oracle replays the GPU's recorded choices and the test checks separately that
+the GPU's own choices agree with the oracle's sampler.
+"""
+import numpy as np
+import pytest
+
+from helpers import gpu_geom, oracle_geom, rel_l2, spec
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import bsgd as OB  # noqa: E402
+from oracle import projector as OP  # noqa: E402
+from oracle import tv as OT  # noqa: E402
+from paper_1903_11874_gb300 import binding as B  # noqa: E402
+from paper_1903_11874_gb300 import synth  # noqa: E402
+
+DEV = "cuda:0"
+RHO = 0.25
+
+_CACHE = {}
+
+
+def problem(name):
+    """(spec, oracle geometry, GPU geometry, y (FP32-rounded), mu)."""
+    if name not in _CACHE:
+        s = spec(name)
+        og, gg = oracle_geom(s), gpu_geom(s)
+        if og.nz > 1:
+            xt = synth.ellipsoid_phantom(og.nx, og.ny, og.nz, 6, seed=0).astype(np.float64)
+        else:
+            xt = synth.ellipse_phantom(og.nx, og.ny, 6, seed=0)
+        y = OP.fp(og, xt.reshape(-1)).reshape(-1).astype(np.float32).astype(np.float64)
+        mu = RHO * OB.step_strip(og, s["N"], 1.0, 30)
+        _CACHE[name] = (s, og, gg, y, mu, xt.reshape(-1))
+    return _CACHE[name]
+
+
+def gpu_run(gg, y, prm, iters, x=None, storage=torch.float32):
+    st = B.State(gg, prm, torch.from_numpy(y.astype(np.float32)).to(DEV))
+    if x is None:
+        x = torch.zeros(gg.n_cols, device=DEV, dtype=storage)
+    st.block_step(x, iters)
+    torch.cuda.synchronize()
+    return st, x
+
+
+def oracle_replay(trace, n_pairs_max, max_views, M, og, prm_o, cells):
+    sels = []
+    for t in trace:
+        np_ = int(t[0])
+        pairs = [(int(t[1 + 2 * p]), int(t[2 + 2 * p])) for p in range(np_)]
+        cl = []
+        for p, (i, _) in enumerate(pairs):
+            if not cells:
+                cl.append(None)
+                continue
+            nv = OP.row_block_views(og, M, i).size
+            base = 1 + 2 * np_ + p * max_views
+            cl.append(np.array(t[base:base + nv], dtype=np.int64))
+        sels.append(OB.Selection(pairs, cl))
+    return sels
+
+
+@pytest.mark.parametrize("kM,kN", [(1, 1), (2, 1), (1, 2), (2, 2)])
+def test_device_sampler_follows_the_spec(kM, kN):
+    s, og, gg, y, mu, _ = problem("paper2d")
+    M, N = s["M"], s["N"]
+    prm = B.SolveParams(alpha=kM / M, gamma=kN / N, step_rule=B.STEP_FIXED, mu=mu, seed=11)
+    st, _ = gpu_run(gg, y, prm, 40)
+    tr = st.read_trace(40)
+    po = OB.Params(M, N, kM / M, kN / N, mu, seed=11)
+    for it in range(40):
+        exp = OB.sample(og, po, it, None, None, None).pairs
+        got = [(int(tr[it, 1 + 2 * p]), int(tr[it, 2 + 2 * p])) for p in range(int(tr[it, 0]))]
+        assert got == exp, it
+
+
+def test_config1_trajectory_matches_oracle():
+    """Config 1: 64^2, 90 x 96 parallel beam, 4 x 4 blocks, alpha = gamma = 1/4,
+    uniform sampling, 50 epochs (800 iterations): final x within 1e-5."""
+    s, og, gg, y, mu, xt = problem("config1")
+    M, N = s["M"], s["N"]
+    iters = 50 * 16
+    prm = B.SolveParams(alpha=0.25, gamma=0.25, step_rule=B.STEP_FIXED, mu=mu, seed=1)
+    st, x = gpu_run(gg, y, prm, iters)
+    ost = OB.bsgd(og, y, OB.Params(M, N, 0.25, 0.25, mu, seed=1), iters)
+    got = x.cpu().double().numpy()
+    assert rel_l2(got, ost.x) <= 1e-5
+    rep = st.query()
+    assert rep["iteration"] == iters
+    assert abs(rep["residual_norm"] - ost.residual_norm()) <= 1e-4 * np.linalg.norm(y)
+    assert rel_l2(got, xt) < 0.13       # and it is a reconstruction
+
+
+def test_several_column_blocks_per_iteration():
+    """alpha = gamma = 1/2 on the paper's 2D set-up: two column blocks share a
+    row block, so r is recomputed after both FPs (the unfused path)."""
+    s, og, gg, y, mu, _ = problem("paper2d")
+    M, N = s["M"], s["N"]
+    prm = B.SolveParams(alpha=0.5, gamma=1.0, step_rule=B.STEP_FIXED, mu=mu, seed=5)
+    _, x = gpu_run(gg, y, prm, 60)
+    x_lit, _ = OB.bsgd_literal(og, y, OB.Params(M, N, 0.5, 1.0, mu, seed=5), 60)
+    assert rel_l2(x.cpu().double().numpy(), x_lit) <= 1e-5
+
+
+@pytest.mark.parametrize("pairs,cells", [(B.PAIRS_UNIFORM, B.CELLS_GEOMETRIC),
+                                         (B.PAIRS_UNIFORM, B.CELLS_UNIFORM),
+                                         (B.PAIRS_RESIDUAL, B.CELLS_NONE),
+                                         (B.PAIRS_RESIDUAL, B.CELLS_GEOMETRIC)])
+def test_importance_sampling_replay_and_choices(pairs, cells):
+    s, og, gg, y, mu, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    iters = 48
+    use_cells = cells != B.CELLS_NONE
+    prm = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu, seed=3,
+                        pair_sampling=pairs, cells=cells, n_cells=4 if use_cells else 1)
+    st, x = gpu_run(gg, y, prm, iters)
+    tr = st.read_trace(iters)
+    names = {B.CELLS_NONE: "none", B.CELLS_GEOMETRIC: "geometric", B.CELLS_UNIFORM: "uniform"}
+    po = OB.Params(M, N, 1 / M, 1 / N, mu, seed=3,
+                   pair_sampling="uniform" if pairs == B.PAIRS_UNIFORM else "residual",
+                   cells=names[cells], n_cells=4 if use_cells else 1)
+    sels = oracle_replay(tr, 1, gg.info.max_views_per_block, M, og, po, use_cells)
+    ost = OB.BSGDState(og, y, po)
+    agree = total = 0
+    for sel in sels:
+        own = OB.sample(og, po, ost.it, ost.r, ost.bands, ost.cell_w)
+        total += 1
+        agree += own.pairs == sel.pairs and all(
+            (a is None and b is None) or np.array_equal(a, b) for a, b in zip(own.cells, sel.cells))
+        ost.step(sel)
+    assert rel_l2(x.cpu().double().numpy(), ost.x) <= 1e-5
+    # FP32 vs FP64 weights may flip a draw that lands within rounding of a CDF step
+    assert agree >= total - 1
+
+
+def test_power_iteration_matches_oracle():
+    s, og, gg, _, _, _ = problem("cone_small")
+    for j in range(s["N"]):
+        lam_g = B.bsgd_power_iteration(gg, j, 30)
+        lam_o = OB.power_iteration(og, s["N"], j, 30)
+        assert abs(lam_g - lam_o) <= 1e-5 * lam_o
+    # STRIP rule inside the state: mu = rho / max_J lambda_J
+    prm = B.SolveParams(alpha=0.25, gamma=0.25, step_rule=B.STEP_STRIP, rho=RHO, power_iters=30)
+    st = B.State(gg, prm, torch.zeros(gg.n_rows, device=DEV))
+    assert abs(st.query()["mu"] - problem("cone_small")[4]) <= 1e-5 * problem("cone_small")[4]
+
+
+@pytest.mark.parametrize("name", ["config1", "cone_small"])
+def test_tv_prox_matches_oracle(name):
+    s, og, gg, _, _, xt = problem(name)
+    b = xt + 0.1 * synth.normal_array(og.n_cols, 21)
+    kappa = 0.05
+    xg = torch.from_numpy(b.astype(np.float32)).to(DEV)
+    B.bsgd_tv_prox(gg, xg, kappa, 20)
+    shape = og.vol_shape if og.nz > 1 else (og.ny, og.nx)
+    ref = OT.tv_prox(b.astype(np.float32).astype(np.float64).reshape(shape), kappa, 20).reshape(-1)
+    assert rel_l2(xg.cpu().double().numpy(), ref) <= 1e-5
+
+
+def test_bsgd_tv_matches_oracle():
+    """Algorithm 4: the prox runs after every 1/(alpha gamma) iterations."""
+    s, og, gg, y, mu, _ = problem("config1")
+    M, N = s["M"], s["N"]
+    prm = B.SolveParams(alpha=0.25, gamma=0.25, step_rule=B.STEP_FIXED, mu=mu, seed=2,
+                        tv_lambda=2.0, tv_iters=10)
+    _, x = gpu_run(gg, y, prm, 48)
+    ost = OB.bsgd(og, y, OB.Params(M, N, 0.25, 0.25, mu, seed=2, tv_lambda=2.0, tv_iters=10), 48)
+    assert rel_l2(x.cpu().double().numpy(), ost.x) <= 1e-5
+
+
+@pytest.mark.parametrize("storage", [B.BF16, B.F16])
+def test_reduced_precision_storage(storage):
+    """Sinogram, image and solver state stored in BF16 / FP16 with FP32 ray sums
+    and accumulation: within 1e-2 of the FP64 oracle after 50 epochs."""
+    s, og, gg, y, mu, _ = problem("config1")
+    M, N = s["M"], s["N"]
+    iters = 50 * 16
+    tdt = torch.bfloat16 if storage == B.BF16 else torch.float16
+    prm = B.SolveParams(alpha=0.25, gamma=0.25, step_rule=B.STEP_FIXED, mu=mu, seed=1,
+                        storage=storage)
+    _, x = gpu_run(gg, y, prm, iters, storage=tdt)
+    ost = OB.bsgd(og, y, OB.Params(M, N, 0.25, 0.25, mu, seed=1), iters)
+    assert rel_l2(x.float().cpu().double().numpy(), ost.x) <= 1e-2
+
+
+def test_solve_with_host_buffers_equals_block_steps():
+    s, og, gg, y, mu, _ = problem("config1")
+    prm = B.SolveParams(alpha=0.25, gamma=0.25, epochs=3, step_rule=B.STEP_FIXED, mu=mu, seed=4)
+    yh = y.astype(np.float32)
+    xh = np.zeros(og.n_cols, dtype=np.float32)
+    rep = B.bsgd_solve(gg, prm, yh, xh)
+    _, x = gpu_run(gg, y, prm, 3 * 16)
+    assert rep["iteration"] == 48
+    assert rel_l2(xh, x.cpu().numpy()) <= 1e-6
+
+
+def test_config2_first_iteration():
+    """Config 2 at full size (256^3, 360 x 256^2, 8 x 8 blocks, residual-weighted
+    pairs) in the bench's launch shape. From x = 0 the first iteration gives
+    x_J = mu (A_I^J)^T y for the drawn pair: checked on every voxel of the slab."""
+    s = spec("config2")
+    og, gg = oracle_geom(s), gpu_geom(s)
+    rng = np.random.default_rng(0)
+    y = np.abs(rng.standard_normal(og.n_rows)).astype(np.float32)
+    mu = 1e-6
+    prm = B.SolveParams(alpha=1 / 8, gamma=1 / 8, step_rule=B.STEP_FIXED, mu=mu, seed=9,
+                        pair_sampling=B.PAIRS_RESIDUAL)
+    st, x = gpu_run(gg, y.astype(np.float64), prm, 1)
+    tr = st.read_trace(1)
+    i, j = int(tr[0, 1]), int(tr[0, 2])
+    rows = OP.rows_of_views(og, OP.row_block_views(og, 8, i))
+    blk = OP.column_block(og, 8, j)
+    vox = OP.column_block_voxels(og, 8, j)
+    ref = mu * OP.bp_rows(og, y[rows].astype(np.float64), rows, blk)[vox]
+    got = x.cpu().double().numpy()
+    assert rel_l2(got[vox], ref) <= 1e-5
+    other = np.setdiff1d(np.arange(og.n_cols), vox)
+    assert not got[other].any()
