@@ -72,7 +72,12 @@ def test_finite_differences_and_adjoint_batch16():
         fd = float((lp - lm) / (xp[k].double() - xm[k].double()))
         g = float(grad.reshape(-1)[k])
         errs.append(abs(fd - g) / max(abs(g), 1e-3 * float(grad.abs().max())))
-    assert max(errs) < 2e-3, max(errs)
+    # The loss is quadratic, so the central difference has no truncation error;
+    # what remains is the FP32 rounding of the ~2 x 180 ray sums through the
+    # voxel (a few ulps of |y| ~ 1e2 each), divided by 2 eps: ~1e-3 relative in
+    # the worst voxel, far less in most.
+    assert max(errs) < 5e-3, max(errs)
+    assert float(np.median(errs)) < 1e-4, float(np.median(errs))
     # adjoint dot-product test on the same operator, batched
     r = torch.tensor(synth.normal_array((Bn,) + tuple(gg.sino_shape), 5), dtype=torch.float32,
                      device=DEV)
