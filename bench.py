@@ -46,6 +46,15 @@ UNIT = "GVox-ray/s"
 ALU_OPS_PER_UPDATE = 5
 
 
+# Serving workload: Poisson arrivals (20 / s), request sizes n^3 with (256 / n) mm
+# voxels, views over 360 deg, n x n detector of 1.6 * 256 / n mm, FP32 or BF16
+# storage, 8 x 8 blocks, uniform pairs, epochs per request. The default run
+# serves a bounded stream (16 requests, n <= 256, 2 epochs); --serving full is
+# the whole stream (200 requests, n up to 384, 10 epochs, 160 GB budget).
+SERVE_FULL = dict(n_req=200, sizes=(64, 128, 256, 384), views=(90, 180, 360, 720), epochs=10)
+SERVE_SMALL = dict(n_req=16, sizes=(64, 128, 256), views=(90, 180, 360), epochs=2)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -54,6 +63,7 @@ def parse():
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", default="small", choices=["off", "small", "full"])
     return ap.parse_args()
 
 
@@ -256,6 +266,11 @@ def run_cuda(args):
                "h2d_bytes_per_step": int(gg.n_rows * 4), "d2h_bytes_per_step": int(gg.n_cols * 4),
                "api": "bsgd_solve (1 epoch per call, pinned host y and x, fixed mu)"}
 
+    serving = None
+    if args.serving != "off":
+        serving = serving_leg(B, torch, dev, SERVE_FULL if args.serving == "full" else SERVE_SMALL,
+                              seed=3 + rank)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(y_np, mu, n_iters=2)
@@ -273,11 +288,89 @@ def run_cuda(args):
                        "mu": mu, "residual_norm_end": q1["residual_norm"]},
             "gpu_launches": int(launches), "stages_ms": stages,
             "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Serving: served mixed stream vs the plain single-request FP32 path
+
+def serve_geometry(n, views):
+    h = 256.0 / n
+    return dict(kind="cone3d", nx=n, ny=n, nz=n, dx=h, dy=h, dz=h, n_views=views, nu=n, nv=n,
+                du=1.6 * h, dv=1.6 * h, dso=500.0, dsd=1000.0)
+
+
+def serving_leg(B, torch, dev, cfg, seed=3, rate=20.0, budget=160 << 30):
+    import numpy as np
+    from paper_1903_11874_gb300 import synth
+    rng = np.random.default_rng(seed)
+    n_req = cfg["n_req"]
+    reqs = [(int(rng.choice(cfg["sizes"])), int(rng.choice(cfg["views"])),
+             B.F32 if rng.random() < 0.5 else B.BF16) for _ in range(n_req)]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    data = {}
+    phantoms = {}
+    for n, v, _ in reqs:
+        if (n, v) in data:
+            continue
+        if n not in phantoms:
+            phantoms[n] = torch.from_numpy(
+                (synth.ellipsoid_phantom(n, n, n, 10, seed=0) * KAPPA).reshape(-1)).to(dev)
+        gg = B.Geometry(M=M, N=N, **serve_geometry(n, v))
+        p = torch.zeros(gg.n_rows, device=dev)
+        B.bsgd_forward_project(gg, phantoms[n], p)
+        data[(n, v)] = p.cpu().numpy().astype(np.float32)
+        del gg
+
+    def params(storage, k):
+        return B.SolveParams(alpha=1 / M, gamma=1 / N, epochs=cfg["epochs"], rho=RHO,
+                             power_iters=8, pair_sampling=B.PAIRS_UNIFORM, storage=storage,
+                             seed=100 + k)
+
+    # served: submit at the arrival times, continuous batching on the GPU
+    srv = B.Server(budget_bytes=budget, max_slots=16, device=torch.cuda.current_device())
+    t0 = time.perf_counter()
+    ids = []
+    for k, (n, v, st) in enumerate(reqs):
+        delay = t0 + arrivals[k] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(srv.submit(serve_geometry(n, v), M, N, params(st, k), data[(n, v)]))
+    for i in ids:
+        srv.wait(i, timeout_ms=3600 * 1000)
+    makespan = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    served = {"p50_ms": round(stats["p50_ms"], 1), "p99_ms": round(stats["p99_ms"], 1),
+              "mean_ms": round(stats["mean_ms"], 1),
+              "value": round(stats["updates"] / makespan / 1e9, 2), "unit": UNIT,
+              "peak_resident": stats["peak_resident"], "peak_gb": round(stats["peak_bytes"] / 1e9, 1),
+              "rounds": stats["rounds"]}
+    # plain single-request FP32 path, first come first served, same arrivals
+    finish, lat, upd = 0.0, [], 0
+    for k, (n, v, _) in enumerate(reqs):
+        gg = B.Geometry(M=M, N=N, **serve_geometry(n, v))
+        x = np.zeros(gg.n_cols, dtype=np.float32)
+        ts = time.perf_counter()
+        rep = B.bsgd_solve(gg, params(B.F32, k), data[(n, v)], x)
+        dur = time.perf_counter() - ts
+        upd += rep["updates"]
+        finish = max(finish, arrivals[k]) + dur
+        lat.append(1e3 * (finish - arrivals[k]))
+        del gg
+    lat.sort()
+    pct = lambda q: lat[min(len(lat) - 1, int(round(q * (len(lat) - 1))))]
+    plain = {"p50_ms": round(pct(0.5), 1), "p99_ms": round(pct(0.99), 1),
+             "value": round(upd / max(finish, 1e-9) / 1e9, 2), "unit": UNIT}
+    return {"workload": "Poisson %g req/s, %d requests, n^3 in %s, views in %s, FP32/BF16 mixed, "
+                        "8x8 blocks, %d epochs" % (rate, n_req, list(cfg["sizes"]),
+                                                    list(cfg["views"]), cfg["epochs"]),
+            "served": served, "plain_fp32": plain}
 
 
 # ---------------------------------------------------------------------------

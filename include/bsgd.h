@@ -316,6 +316,70 @@ bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_params *p,
                        const void *y, bsgd_dtype yt, void *x, bsgd_dtype xt,
                        bsgd_report *out, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of many reconstructions on one GPU          */
+/*
+ * The paper's master node feeds sub-blocks to whichever GPU is free (Sec. 2,
+ * Fig. 1); here one GPU runs many independent reconstructions at once. A server
+ * admits requests of any geometry, size and storage type while their device
+ * memory fits a byte budget, keeps each admitted request's state (x, z^j, r,
+ * snapshots, sampling tables) resident, and advances all resident requests
+ * together: one round = one BSGD iteration of every resident request, launched
+ * as a captured CUDA graph of persistent kernels that share the GPU among the
+ * requests' rays. Requests that arrive while others run are admitted as slots
+ * and budget free up; finished requests leave without stopping the others.
+ * Each request's result equals its result alone up to the order of float
+ * atomics (its sampling depends only on its own seed and iteration count).
+ * Requests must draw one column block per iteration (gamma N = 1) and use no TV
+ * prox; others are rejected at submit.
+ */
+typedef struct bsgd_server bsgd_server;
+
+typedef struct {
+    size_t budget_bytes;      /* device memory the resident requests may hold    */
+    int max_slots;            /* resident requests at most (<= 64)               */
+    int device;               /* CUDA device                                     */
+} bsgd_server_params;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed, queued, resident;
+    int peak_resident;
+    size_t bytes_resident, peak_bytes;
+    double p50_ms, p99_ms, mean_ms, max_ms; /* submit -> result latency, completed requests */
+    int64_t updates;          /* voxel-ray updates of completed requests         */
+    double busy_s;            /* wall time with at least one request resident    */
+    int64_t rounds;
+} bsgd_server_stats;
+
+/*
+ * Device bytes a request holds while resident (its state, image, geometry
+ * tables and the transient set-up buffers), as the admission test counts it.
+ * Host-only; no GPU needed.
+ */
+bsgd_status bsgd_request_bytes(const bsgd_geometry_desc *desc, int M, int N,
+                               const bsgd_solve_params *p, size_t *out);
+
+/* Start a server (its scheduler threads, streams and round graph). */
+bsgd_status bsgd_server_create(const bsgd_server_params *p, bsgd_server **out);
+/* Stop: cancels queued requests, waits (bounded) for resident ones, frees all. */
+bsgd_status bsgd_server_destroy(bsgd_server *s);
+
+/*
+ * Queue a reconstruction: y (host, n_rows elements of type yt) is copied before
+ * the call returns; the result (n_cols float32 values) is written to x_out
+ * (host, caller-owned, valid until the request completes or fails).
+ * Errors: INVALID_ARG (bad geometry / params, gamma N != 1, TV), BUDGET (the
+ * request alone exceeds the budget), STATE (server stopping).
+ */
+bsgd_status bsgd_server_submit(bsgd_server *s, const bsgd_geometry_desc *desc, int M, int N,
+                               const bsgd_solve_params *p, const void *y, bsgd_dtype yt,
+                               float *x_out, int64_t *id);
+/* Wait up to timeout_ms for request id; TIMEOUT if it is still running. */
+bsgd_status bsgd_server_wait(bsgd_server *s, int64_t id, int timeout_ms, bsgd_report *out);
+/* *done = 1 if request id finished (successfully or not). */
+bsgd_status bsgd_server_poll(bsgd_server *s, int64_t id, int *done);
+bsgd_status bsgd_server_get_stats(bsgd_server *s, bsgd_server_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,8 @@ EXPORTS = (
     "bsgd_power_iteration", "bsgd_tv_prox", "bsgd_state_create", "bsgd_state_destroy",
     "bsgd_block_step", "bsgd_state_query", "bsgd_trace_stride", "bsgd_state_read_trace",
     "bsgd_state_set_replay", "bsgd_state_profile", "bsgd_state_read_profile", "bsgd_solve",
+    "bsgd_request_bytes", "bsgd_server_create", "bsgd_server_destroy", "bsgd_server_submit",
+    "bsgd_server_wait", "bsgd_server_poll", "bsgd_server_get_stats",
 )
 STAGES = ("sample", "fp", "residual", "bp", "update", "tv")
 
@@ -87,6 +89,24 @@ class Report(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerParams(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+        ("failed", ctypes.c_int64), ("queued", ctypes.c_int64), ("resident", ctypes.c_int64),
+        ("peak_resident", ctypes.c_int), ("bytes_resident", ctypes.c_size_t),
+        ("peak_bytes", ctypes.c_size_t), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+        ("mean_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("updates", ctypes.c_int64),
+        ("busy_s", ctypes.c_double), ("rounds", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _LIB = None
 _vp, _i32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)
 
@@ -132,6 +152,16 @@ def load(build_if_missing: bool = True):
         "bsgd_state_profile": (st, [_vp, ctypes.c_int]),
         "bsgd_state_read_profile": (st, [_vp, P(Profile), _vp]),
         "bsgd_solve": (st, [_vp, P(SolveParamsC), _vp, st, _vp, st, P(Report), _vp]),
+        "bsgd_request_bytes": (st, [P(GeometryDesc), ctypes.c_int, ctypes.c_int, P(SolveParamsC),
+                                    P(ctypes.c_size_t)]),
+        "bsgd_server_create": (st, [P(ServerParams), P(_vp)]),
+        "bsgd_server_destroy": (st, [_vp]),
+        "bsgd_server_submit": (st, [_vp, P(GeometryDesc), ctypes.c_int, ctypes.c_int,
+                                    P(SolveParamsC), _vp, st, ctypes.POINTER(ctypes.c_float),
+                                    P(ctypes.c_int64)]),
+        "bsgd_server_wait": (st, [_vp, ctypes.c_int64, ctypes.c_int, P(Report)]),
+        "bsgd_server_poll": (st, [_vp, ctypes.c_int64, P(ctypes.c_int)]),
+        "bsgd_server_get_stats": (st, [_vp, P(ServerStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +219,19 @@ def _ids(ids):
 # ---------------------------------------------------------------------------
 # Geometry
 
+def make_desc(kind, nx, ny, nz, dx, dy, dz, n_views, nu, nv, du, dv, dso=0.0, dsd=0.0,
+              angles=None, view_block=None):
+    """A bsgd_geometry_desc and the arrays it points to (keep them alive)."""
+    ang = None if angles is None else np.ascontiguousarray(angles, dtype=np.float64)
+    vb = None if view_block is None else np.ascontiguousarray(view_block, dtype=np.int32)
+    d = GeometryDesc(KINDS[kind] if isinstance(kind, str) else int(kind), int(nx), int(ny), int(nz),
+                     float(dx), float(dy), float(dz), int(n_views),
+                     None if ang is None else ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     int(nu), int(nv), float(du), float(dv), float(dso), float(dsd),
+                     None if vb is None else vb.ctypes.data_as(_i32p))
+    return d, (ang, vb)
+
+
 class Geometry:
     """Owning handle of a bsgd_geometry (bsgd_geometry_create / _destroy)."""
 
@@ -200,13 +243,8 @@ class Geometry:
         self.dx, self.dy, self.dz = float(dx), float(dy), float(dz)
         self.n_views, self.nu, self.nv = int(n_views), int(nu), int(nv)
         self.du, self.dv, self.dso, self.dsd = float(du), float(dv), float(dso), float(dsd)
-        self._angles = None if angles is None else np.ascontiguousarray(angles, dtype=np.float64)
-        self._vb = None if view_block is None else np.ascontiguousarray(view_block, dtype=np.int32)
-        d = GeometryDesc(KINDS[kind] if isinstance(kind, str) else int(kind), self.nx, self.ny,
-                         self.nz, self.dx, self.dy, self.dz, self.n_views,
-                         None if self._angles is None else self._angles.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                         self.nu, self.nv, self.du, self.dv, self.dso, self.dsd,
-                         None if self._vb is None else self._vb.ctypes.data_as(_i32p))
+        d, self._keep = make_desc(kind, nx, ny, nz, dx, dy, dz, n_views, nu, nv, du, dv, dso, dsd,
+                                  angles, view_block)
         h = ctypes.c_void_p()
         _check(lib.bsgd_geometry_create(ctypes.byref(d), int(M), int(N), ctypes.byref(h)))
         self.handle = h
@@ -419,3 +457,71 @@ def bsgd_solve(geom, params: SolveParams, y, x, stream=None) -> dict:
     _check(load().bsgd_solve(geom.handle, ctypes.byref(pc), _any_ptr(y), _any_dtype(y),
                              _any_ptr(x), _any_dtype(x), ctypes.byref(rep), _stream(stream)))
     return rep.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# Serving
+
+def bsgd_request_bytes(geo: dict, M: int, N: int, params: SolveParams) -> int:
+    """Device bytes a request holds while resident (the admission model)."""
+    d, _keep = make_desc(**geo)
+    pc = params.c()
+    out = ctypes.c_size_t()
+    _check(load().bsgd_request_bytes(ctypes.byref(d), int(M), int(N), ctypes.byref(pc),
+                                     ctypes.byref(out)))
+    return int(out.value)
+
+
+class Server:
+    """Owning handle of a bsgd_server: submit reconstructions, wait for them."""
+
+    def __init__(self, budget_bytes, max_slots=16, device=0):
+        h = ctypes.c_void_p()
+        prm = ServerParams(int(budget_bytes), int(max_slots), int(device))
+        _check(load().bsgd_server_create(ctypes.byref(prm), ctypes.byref(h)))
+        self.handle = h
+        self._pending = {}
+
+    def submit(self, geo: dict, M: int, N: int, params: SolveParams, y: np.ndarray) -> int:
+        """Queue a reconstruction of y (host float32 / float16 array); returns its id."""
+        d, keep = make_desc(**geo)
+        pc = params.c()
+        y = np.ascontiguousarray(y)
+        yt = {np.dtype(np.float32): F32, np.dtype(np.float16): F16}[y.dtype]
+        nx, ny, nz = int(geo["nx"]), int(geo["ny"]), int(geo["nz"])
+        x = np.zeros(nx * ny * nz, dtype=np.float32)
+        rid = ctypes.c_int64()
+        _check(load().bsgd_server_submit(self.handle, ctypes.byref(d), int(M), int(N),
+                                         ctypes.byref(pc), ctypes.c_void_p(y.ctypes.data), yt,
+                                         x.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         ctypes.byref(rid)))
+        self._pending[rid.value] = (x, keep)
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout_ms: int = 600000):
+        """(x, report) once request rid is done; BSGDError(TIMEOUT) if not in time."""
+        rep = Report()
+        _check(load().bsgd_server_wait(self.handle, int(rid), int(timeout_ms), ctypes.byref(rep)))
+        x, _keep = self._pending[rid]
+        return x, rep.as_dict()
+
+    def poll(self, rid: int) -> bool:
+        done = ctypes.c_int()
+        _check(load().bsgd_server_poll(self.handle, int(rid), ctypes.byref(done)))
+        return bool(done.value)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().bsgd_server_get_stats(self.handle, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _check(load().bsgd_server_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -62,6 +62,7 @@ struct DeviceGeom {
     const int *block_nviews;   // M
     const int *plane_start;    // N + 1 planes along the block axis
     const int *view_block;     // n_views
+    const unsigned char *view_yfast;  // n_views: 1 if the view's rays run mostly along x
     int nx, ny, nz;
     float hx, hy, hz;
     int nu, nv, n_views;
@@ -93,6 +94,7 @@ struct bsgd_geometry {
     int *d_block_nviews = nullptr;
     int *d_plane_start = nullptr;
     int *d_view_block = nullptr;
+    unsigned char *d_view_yfast = nullptr;
     bsgd::DeviceGeom dg{};
 
     int64_t n_rows() const { return (int64_t)desc.n_views * desc.nv * desc.nu; }
@@ -137,7 +139,7 @@ bsgd_status zero_rows(const bsgd_geometry *g, const int *row_ids, int n_rb, void
                       bsgd_dtype yt, cudaStream_t st);
 
 // Tile of rays per CTA.
-constexpr int kTileU3 = 16, kTileV3 = 8;   // 3D: 2 x 2 warps of 8 u x 4 v rays
+constexpr int kTileU3 = 32, kTileV3 = 4;   // 3D: 4 warps, each 32 u of one detector row
 constexpr int kTileU2 = 128, kTileV2 = 1;  // 2D: 4 warps of 32 u rays
 inline int tile_u(const bsgd_geometry *g) { return g->desc.nv > 1 ? kTileU3 : kTileU2; }
 inline int tile_v(const bsgd_geometry *g) { return g->desc.nv > 1 ? kTileV3 : kTileV2; }
@@ -177,6 +179,11 @@ struct SolveDev {
     const int *cells;  // kMaxPairs x max_views chosen cells (-1: whole view)
     int n_cells;       // 1 (no cells), 2 or 4
     const double *mu;  // step
+    // y-fastest copies used by the views whose rays run mostly along x (3D
+    // only; null otherwise): adjacent rays of a warp then gather and scatter
+    // adjacent addresses
+    void *xT;          // image, [z][x][y], storage type
+    float *gT;         // their part of the aggregated gradient, [z][x][y]
 };
 
 // Sub-detector cell rectangle (Fig. 2): halves in u for 2 cells, quadrants
@@ -198,5 +205,72 @@ bsgd_status launch_bp_solve(const bsgd_geometry *g, const SolveDev &S, bsgd_dtyp
                             int max_pairs, int max_tiles, cudaStream_t st);
 bsgd_status launch_count_cells(const bsgd_geometry *g, int j, int n_cells,
                                unsigned long long *d_counts, cudaStream_t st);
+
+}  // namespace bsgd
+
+namespace bsgd {
+
+struct SampleArgs {
+    DeviceGeom G;
+    Work *work;
+    int *cells;                 // kMaxPairs x max_views
+    int64_t *iter;
+    uint64_t seed;
+    int pairs_mode, cells_mode, n_cells, kM, kN;
+    const double *S;            // M x nv
+    const int *wband;           // M x N x 2
+    const double *cw;           // N x n_views x n_cells
+    const int32_t *replay;      // replay_n x stride
+    int64_t replay_start, replay_n;
+    int32_t *trace;             // trace_cap x stride
+    int64_t trace_cap;
+    int stride;
+    const unsigned long long *counts;  // N x n_views x n_cells
+    unsigned long long *updates;
+};
+
+// ---------------------------------------------------------------------------
+// Serving: one entry per resident request of a server (device table)
+
+struct ReqDesc {
+    DeviceGeom G;
+    SolveDev S;
+    SampleArgs A;
+    void *x;                 // image (storage type)
+    void *xlo;               // low-order image term (16-bit storage) or null
+    int dtype;               // storage type
+    int max_tiles;           // detector tiles of the largest band of one pair
+    int active;
+    int pad;
+    int64_t work_begin;      // first FP / BP work item of this request in a round
+    int64_t work_count;      // max_tiles * max_views * pairs
+    int64_t max_block_cols;  // voxels of the largest column block
+};
+
+struct RoundCtl {
+    unsigned long long fp_next, bp_next;   // persistent-kernel work counters
+    int n;                                 // table entries in use
+    int pad;
+    int64_t total_items;                   // FP / BP work items of the round
+};
+
+// Fill a request descriptor from a live state (solver.cu).
+bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out);
+// Device bytes state_create allocates for this geometry and these parameters,
+// and the transient set-up buffers on top (solver.cu).
+size_t state_bytes(const bsgd_geometry_desc &d, int M, int N, const bsgd_solve_params &p,
+                   size_t *transient);
+bsgd_status validate_desc(const bsgd_geometry_desc *d, int M, int N);
+bsgd_status convert(const void *in, bsgd_dtype it, void *out, bsgd_dtype ot, int64_t n,
+                    cudaStream_t st);
+
+// Round kernels of the server (enqueued once into a captured graph).
+bsgd_status launch_round_sample(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
+                                cudaStream_t st);
+bsgd_status launch_round_fp(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st);
+bsgd_status launch_round_bp(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st);
+bsgd_status launch_round_update(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
+                                cudaStream_t st);
+int round_persistent_grid();
 
 }  // namespace bsgd

@@ -171,6 +171,8 @@ bsgd_status validate(const bsgd_geometry_desc *d, int M, int N) {
 
 }  // namespace
 
+bsgd_status validate_desc(const bsgd_geometry_desc *d, int M, int N) { return validate(d, M, N); }
+
 int tiles_for(const bsgd_geometry *g, const std::vector<int> &views, int j0, int j1, int tu,
               int tv) {
     int best = 0;
@@ -207,6 +209,7 @@ static void free_geometry(bsgd_geometry *g) {
     cudaFree(g->d_block_nviews);
     cudaFree(g->d_plane_start);
     cudaFree(g->d_view_block);
+    cudaFree(g->d_view_yfast);
     delete g;
 }
 
@@ -328,6 +331,11 @@ extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int 
         bn[i] = (int)g->block_views[i].size();
         for (int k = 0; k < bn[i]; ++k) bv[(size_t)i * g->max_views + k] = g->block_views[i][k];
     }
+    // views whose rays run mostly along x (|cos| > |sin| of the view angle)
+    // use the y-fastest copies of the solver state (volumes only)
+    std::vector<unsigned char> yfast(d.n_views, 0);
+    for (int a = 0; a < d.n_views && d.nz > 1; ++a)
+        yfast[a] = std::fabs(std::cos(g->angles[a])) > std::fabs(std::sin(g->angles[a])) ? 1 : 0;
     bsgd_status st = BSGD_OK;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -338,7 +346,8 @@ extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int 
         (st = upload((void **)&g->d_block_nviews, bn.data(), bn.size() * sizeof(int))) ||
         (st = upload((void **)&g->d_plane_start, g->plane_start.data(), (N + 1) * sizeof(int))) ||
         (st = upload((void **)&g->d_view_block, g->view_block.data(),
-                     g->view_block.size() * sizeof(int)))) {
+                     g->view_block.size() * sizeof(int))) ||
+        (st = upload((void **)&g->d_view_yfast, yfast.data(), yfast.size()))) {
         free_geometry(g);
         return st;
     }
@@ -349,6 +358,7 @@ extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int 
     dg.block_nviews = g->d_block_nviews;
     dg.plane_start = g->d_plane_start;
     dg.view_block = g->d_view_block;
+    dg.view_yfast = g->d_view_yfast;
     dg.nx = d.nx;
     dg.ny = d.ny;
     dg.nz = d.nz;

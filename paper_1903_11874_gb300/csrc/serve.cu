@@ -1,0 +1,524 @@
+// Serving: continuous batching of BSGD reconstructions on one GPU.
+//
+// Two host threads drive the GPU:
+//   admission  takes queued requests in arrival order while slots and the
+//              byte budget allow, builds each one's geometry and solver state
+//              (power-iteration step included) on its own stream, and hands
+//              the ready request to the round thread;
+//   rounds     keeps a device table of the resident requests and replays one
+//              captured CUDA graph per round: sampler of every request, then
+//              persistent FP and BP kernels that share all requests' detector
+//              tiles through atomic work counters, then every request's block
+//              update. After the last iteration of a request the round thread
+//              copies its image out, and once that copy has finished it frees
+//              the request and releases its budget.
+// The graph never changes: the kernels read the table and the number of
+// entries from device memory, which the round thread rewrites between rounds
+// when requests join or leave.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+#include "bsgd_internal.h"
+
+using namespace bsgd;
+
+namespace {
+
+double now_s() {
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+enum ReqStatus { kQueued, kAdmitting, kReady, kResident, kFinishing, kDone, kFailed };
+
+struct Request {
+    int64_t id = 0;
+    bsgd_geometry_desc desc{};
+    std::vector<double> angles;
+    std::vector<int32_t> view_block;
+    int M = 1, N = 1;
+    bsgd_solve_params p{};
+    std::vector<char> y;          // host copy of the data
+    bsgd_dtype yt = BSGD_F32;
+    float *x_out = nullptr;       // caller's result buffer
+    size_t bytes = 0;             // budget charged while admitted
+    int64_t target = 0, done = 0; // iterations
+    ReqStatus status = kQueued;
+    std::string error;
+    bsgd_geometry *g = nullptr;
+    bsgd_state *st = nullptr;
+    void *x = nullptr;            // device image (storage type)
+    float *xf = nullptr;          // device float copy for the result
+    float *stage = nullptr;       // pinned host staging of the result
+    unsigned long long *upd_host = nullptr;  // pinned
+    cudaEvent_t ev = nullptr;
+    double t_submit = 0, t_done = 0;
+    bsgd_report rep{};
+};
+
+}  // namespace
+
+struct bsgd_server {
+    bsgd_server_params prm{};
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Request *> queue;
+    std::vector<Request *> ready, resident, finishing;
+    std::map<int64_t, Request *> all;
+    int64_t next_id = 1;
+    int admitting = 0;
+    size_t bytes = 0, peak_bytes = 0;
+    bool stopping = false;
+    std::thread admit_thr, round_thr;
+    cudaStream_t round_stream = nullptr, admit_stream = nullptr;
+    ReqDesc *d_table = nullptr;
+    RoundCtl *d_ctl = nullptr;
+    ReqDesc *h_table = nullptr;   // pinned
+    RoundCtl *h_ctl = nullptr;    // pinned
+    cudaGraphExec_t graph = nullptr;
+    int grid = 0;
+    // stats
+    int64_t submitted = 0, admitted = 0, completed = 0, failed = 0, rounds = 0;
+    int peak_resident = 0;
+    std::vector<double> latencies_ms;
+    int64_t updates = 0;
+    double busy_s = 0, busy_since = -1;
+    std::string thread_error;
+};
+
+namespace {
+
+void free_request_gpu(Request *r) {
+    if (r->st) bsgd_state_destroy(r->st);
+    if (r->g) bsgd_geometry_destroy(r->g);
+    cudaFree(r->x);
+    cudaFree(r->xf);
+    if (r->stage) cudaFreeHost(r->stage);
+    if (r->upd_host) cudaFreeHost(r->upd_host);
+    if (r->ev) cudaEventDestroy(r->ev);
+    r->st = nullptr;
+    r->g = nullptr;
+    r->x = r->xf = nullptr;
+    r->stage = nullptr;
+    r->upd_host = nullptr;
+    r->ev = nullptr;
+}
+
+// Build geometry, state and buffers of one request on the admission stream.
+bsgd_status admit_one(bsgd_server *S, Request *r) {
+    BSGD_TRY(bsgd_geometry_create(&r->desc, r->M, r->N, &r->g));
+    const int64_t R = r->g->n_rows(), C = r->g->n_cols();
+    const size_t ys = dtype_size(r->yt), es = dtype_size((bsgd_dtype)r->p.storage);
+    void *dy = nullptr;
+    BSGD_CUDA(cudaMalloc(&dy, R * ys));
+    cudaError_t e = cudaMemcpyAsync(dy, r->y.data(), R * ys, cudaMemcpyHostToDevice, S->admit_stream);
+    bsgd_status st = e == cudaSuccess ? BSGD_OK : cuda_fail(e, "copy of y");
+    if (!st) st = bsgd_state_create(r->g, &r->p, dy, r->yt, S->admit_stream, &r->st);
+    cudaStreamSynchronize(S->admit_stream);
+    cudaFree(dy);
+    BSGD_TRY(st);
+    r->y.clear();
+    r->y.shrink_to_fit();
+    BSGD_CUDA(cudaMalloc(&r->x, C * es));
+    BSGD_CUDA(cudaMalloc((void **)&r->xf, C * 4));
+    BSGD_CUDA(cudaMemsetAsync(r->x, 0, C * es, S->admit_stream));
+    BSGD_CUDA(cudaHostAlloc((void **)&r->stage, C * 4, cudaHostAllocDefault));
+    BSGD_CUDA(cudaHostAlloc((void **)&r->upd_host, 8, cudaHostAllocDefault));
+    BSGD_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+    BSGD_CUDA(cudaStreamSynchronize(S->admit_stream));
+    ReqDesc tmp;
+    BSGD_TRY(state_descriptor(r->st, r->x, &tmp));   // rejects what rounds cannot run
+    return BSGD_OK;
+}
+
+void admission_loop(bsgd_server *S) {
+    cudaSetDevice(S->prm.device);
+    for (;;) {
+        Request *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] {
+                if (S->stopping) return true;
+                if (S->queue.empty()) return false;
+                const int live = (int)(S->resident.size() + S->ready.size()) + S->admitting;
+                return live < S->prm.max_slots && S->bytes + S->queue.front()->bytes <= S->prm.budget_bytes;
+            });
+            if (S->stopping) return;
+            r = S->queue.front();
+            S->queue.pop_front();
+            r->status = kAdmitting;
+            S->admitting++;
+            S->bytes += r->bytes;
+            S->peak_bytes = std::max(S->peak_bytes, S->bytes);
+        }
+        bsgd_status st = admit_one(S, r);
+        std::string err = st ? bsgd_last_error() : "";
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->admitting--;
+            if (st) {
+                r->status = kFailed;
+                r->error = err;
+                r->t_done = now_s();
+                S->failed++;
+                S->bytes -= r->bytes;
+            } else {
+                r->status = kReady;
+                S->ready.push_back(r);
+                S->admitted++;
+            }
+        }
+        if (st) free_request_gpu(r);
+        S->cv.notify_all();
+    }
+}
+
+bsgd_status build_graph(bsgd_server *S) {
+    cudaGraph_t graph = nullptr;
+    BSGD_CUDA(cudaStreamBeginCapture(S->round_stream, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(&S->d_ctl->fp_next, 0, 2 * sizeof(unsigned long long), S->round_stream);
+    bsgd_status st = launch_round_sample(S->d_table, S->d_ctl, S->prm.max_slots, S->round_stream);
+    if (!st) st = launch_round_fp(S->d_table, S->d_ctl, S->grid, S->round_stream);
+    if (!st) st = launch_round_bp(S->d_table, S->d_ctl, S->grid, S->round_stream);
+    if (!st) st = launch_round_update(S->d_table, S->d_ctl, S->prm.max_slots, S->round_stream);
+    cudaError_t e = cudaStreamEndCapture(S->round_stream, &graph);
+    BSGD_TRY(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&S->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return BSGD_OK;
+}
+
+// Rewrite the device table from the resident list (called with no round in
+// flight: the round stream is synchronised first).
+bsgd_status upload_table(bsgd_server *S) {
+    BSGD_CUDA(cudaStreamSynchronize(S->round_stream));
+    int64_t begin = 0;
+    int n = 0;
+    for (Request *r : S->resident) {
+        ReqDesc d;
+        BSGD_TRY(state_descriptor(r->st, r->x, &d));
+        d.work_begin = begin;
+        begin += d.work_count;
+        S->h_table[n++] = d;
+    }
+    S->h_ctl->n = n;
+    S->h_ctl->total_items = begin;
+    S->h_ctl->fp_next = S->h_ctl->bp_next = 0;
+    if (n) BSGD_CUDA(cudaMemcpyAsync(S->d_table, S->h_table, sizeof(ReqDesc) * n,
+                                     cudaMemcpyHostToDevice, S->round_stream));
+    BSGD_CUDA(cudaMemcpyAsync(S->d_ctl, S->h_ctl, sizeof(RoundCtl), cudaMemcpyHostToDevice,
+                              S->round_stream));
+    BSGD_CUDA(cudaStreamSynchronize(S->round_stream));
+    return BSGD_OK;
+}
+
+// After a request's last iteration: its image to the host, asynchronously.
+bsgd_status start_finish(bsgd_server *S, Request *r) {
+    const int64_t C = r->g->n_cols();
+    BSGD_TRY(convert(r->x, (bsgd_dtype)r->p.storage, r->xf, BSGD_F32, C, S->round_stream));
+    BSGD_CUDA(cudaMemcpyAsync(r->stage, r->xf, C * 4, cudaMemcpyDeviceToHost, S->round_stream));
+    ReqDesc d;
+    BSGD_TRY(state_descriptor(r->st, r->x, &d));
+    BSGD_CUDA(cudaMemcpyAsync(r->upd_host, d.A.updates, 8, cudaMemcpyDeviceToHost, S->round_stream));
+    BSGD_CUDA(cudaEventRecord(r->ev, S->round_stream));
+    return BSGD_OK;
+}
+
+void round_loop(bsgd_server *S) {
+    cudaSetDevice(S->prm.device);
+    bool dirty = true;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait_for(lk, std::chrono::milliseconds(S->resident.empty() && S->finishing.empty() ? 20 : 0), [&] {
+                return S->stopping || !S->ready.empty() || !S->resident.empty() || !S->finishing.empty();
+            });
+            if (S->stopping && S->ready.empty() && S->resident.empty() && S->finishing.empty()) break;
+            while (!S->ready.empty() && (int)S->resident.size() < S->prm.max_slots) {
+                Request *r = S->ready.front();
+                S->ready.erase(S->ready.begin());
+                r->status = kResident;
+                S->resident.push_back(r);
+                dirty = true;
+            }
+            S->peak_resident = std::max(S->peak_resident, (int)S->resident.size());
+            if (!S->resident.empty() && S->busy_since < 0) S->busy_since = now_s();
+        }
+        if (dirty) {
+            bsgd_status st = upload_table(S);
+            if (st) {
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->thread_error = bsgd_last_error();
+                for (Request *r : S->resident) {
+                    r->status = kFailed;
+                    r->error = S->thread_error;
+                    r->t_done = now_s();
+                    S->failed++;
+                }
+                S->resident.clear();
+                S->cv.notify_all();
+                continue;
+            }
+            dirty = false;
+        }
+        if (!S->resident.empty()) {
+            cudaGraphLaunch(S->graph, S->round_stream);
+            S->rounds++;
+            std::vector<Request *> leaving;
+            for (Request *r : S->resident)
+                if (++r->done >= r->target) leaving.push_back(r);
+            for (Request *r : leaving) {
+                bsgd_status st = start_finish(S, r);
+                std::lock_guard<std::mutex> lk(S->mu);
+                S->resident.erase(std::find(S->resident.begin(), S->resident.end(), r));
+                if (st) {
+                    r->status = kFailed;
+                    r->error = bsgd_last_error();
+                    r->t_done = now_s();
+                    S->failed++;
+                } else {
+                    r->status = kFinishing;
+                    S->finishing.push_back(r);
+                }
+                dirty = true;
+            }
+            // keep at most a few rounds in flight so completions are seen early
+            if (S->rounds % 4 == 0) cudaStreamSynchronize(S->round_stream);
+        } else {
+            cudaStreamSynchronize(S->round_stream);
+        }
+        // retire finished requests whose result copy has completed
+        std::vector<Request *> done;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (Request *r : S->finishing)
+                if (cudaEventQuery(r->ev) == cudaSuccess) done.push_back(r);
+            for (Request *r : done) S->finishing.erase(std::find(S->finishing.begin(), S->finishing.end(), r));
+        }
+        for (Request *r : done) {
+            const int64_t C = r->g->n_cols();
+            std::memcpy(r->x_out, r->stage, C * 4);
+            const unsigned long long upd = *r->upd_host;
+            free_request_gpu(r);
+            std::lock_guard<std::mutex> lk(S->mu);
+            r->t_done = now_s();
+            r->rep.iteration = r->target;
+            r->rep.updates = (int64_t)upd;
+            r->status = kDone;
+            S->completed++;
+            S->updates += (int64_t)upd;
+            S->latencies_ms.push_back(1e3 * (r->t_done - r->t_submit));
+            S->bytes -= r->bytes;
+        }
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            if (S->resident.empty() && S->ready.empty() && S->finishing.empty() && S->busy_since >= 0) {
+                S->busy_s += now_s() - S->busy_since;
+                S->busy_since = -1;
+            }
+        }
+        if (!done.empty()) S->cv.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" bsgd_status bsgd_request_bytes(const bsgd_geometry_desc *desc, int M, int N,
+                                          const bsgd_solve_params *p, size_t *out) {
+    if (!desc || !p || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    BSGD_TRY(validate_desc(desc, M, N));
+    if (!dtype_ok(p->storage)) return fail(BSGD_ERR_INVALID_ARG, "bad storage dtype");
+    size_t transient = 0;
+    size_t b = state_bytes(*desc, M, N, *p, &transient);
+    const size_t C = (size_t)desc->nx * desc->ny * desc->nz;
+    const size_t R = (size_t)desc->n_views * desc->nu * desc->nv;
+    b += C * dtype_size((bsgd_dtype)p->storage) + C * 4;   // image and its float copy
+    transient = std::max(transient, R * 4);                 // the device copy of y
+    *out = b + transient + ((size_t)16 << 20);               // allocation granularity
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_server_create(const bsgd_server_params *p, bsgd_server **out) {
+    if (!p || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (p->max_slots < 1 || p->max_slots > 64) return fail(BSGD_ERR_INVALID_ARG, "max_slots in [1, 64]");
+    if (p->budget_bytes == 0) return fail(BSGD_ERR_INVALID_ARG, "budget_bytes must be > 0");
+    BSGD_CUDA(cudaSetDevice(p->device));
+    bsgd_server *S = new (std::nothrow) bsgd_server();
+    if (!S) return fail(BSGD_ERR_OOM, "host allocation failed");
+    S->prm = *p;
+    auto init = [&]() -> bsgd_status {
+        BSGD_CUDA(cudaStreamCreateWithFlags(&S->round_stream, cudaStreamNonBlocking));
+        BSGD_CUDA(cudaStreamCreateWithFlags(&S->admit_stream, cudaStreamNonBlocking));
+        BSGD_CUDA(cudaMalloc((void **)&S->d_table, sizeof(ReqDesc) * p->max_slots));
+        BSGD_CUDA(cudaMalloc((void **)&S->d_ctl, sizeof(RoundCtl)));
+        BSGD_CUDA(cudaHostAlloc((void **)&S->h_table, sizeof(ReqDesc) * p->max_slots, cudaHostAllocDefault));
+        BSGD_CUDA(cudaHostAlloc((void **)&S->h_ctl, sizeof(RoundCtl), cudaHostAllocDefault));
+        std::memset(S->h_ctl, 0, sizeof(RoundCtl));
+        BSGD_CUDA(cudaMemset(S->d_ctl, 0, sizeof(RoundCtl)));
+        S->grid = round_persistent_grid();
+        BSGD_TRY(build_graph(S));
+        return BSGD_OK;
+    };
+    bsgd_status st = init();
+    if (st) {
+        if (S->graph) cudaGraphExecDestroy(S->graph);
+        cudaFree(S->d_table);
+        cudaFree(S->d_ctl);
+        if (S->h_table) cudaFreeHost(S->h_table);
+        if (S->h_ctl) cudaFreeHost(S->h_ctl);
+        if (S->round_stream) cudaStreamDestroy(S->round_stream);
+        if (S->admit_stream) cudaStreamDestroy(S->admit_stream);
+        delete S;
+        return st;
+    }
+    S->admit_thr = std::thread(admission_loop, S);
+    S->round_thr = std::thread(round_loop, S);
+    *out = S;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_server_destroy(bsgd_server *S) {
+    if (!S) return fail(BSGD_ERR_INVALID_ARG, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stopping = true;
+        for (Request *r : S->queue) {
+            r->status = kFailed;
+            r->error = "server stopped";
+        }
+        S->queue.clear();
+    }
+    S->cv.notify_all();
+    if (S->admit_thr.joinable()) S->admit_thr.join();
+    if (S->round_thr.joinable()) S->round_thr.join();
+    cudaSetDevice(S->prm.device);
+    cudaStreamSynchronize(S->round_stream);
+    for (auto &kv : S->all) {
+        free_request_gpu(kv.second);
+        delete kv.second;
+    }
+    if (S->graph) cudaGraphExecDestroy(S->graph);
+    cudaFree(S->d_table);
+    cudaFree(S->d_ctl);
+    cudaFreeHost(S->h_table);
+    cudaFreeHost(S->h_ctl);
+    cudaStreamDestroy(S->round_stream);
+    cudaStreamDestroy(S->admit_stream);
+    delete S;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_server_submit(bsgd_server *S, const bsgd_geometry_desc *desc, int M,
+                                          int N, const bsgd_solve_params *p, const void *y,
+                                          bsgd_dtype yt, float *x_out, int64_t *id) {
+    if (!S || !desc || !p || !y || !x_out || !id) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (!dtype_ok(yt)) return fail(BSGD_ERR_INVALID_ARG, "bad y dtype");
+    size_t bytes = 0;
+    BSGD_TRY(bsgd_request_bytes(desc, M, N, p, &bytes));
+    const int kN = std::max(1, (int)std::lround(p->gamma * N));
+    if (kN != 1) return fail(BSGD_ERR_INVALID_ARG, "serving needs gamma * N == 1");
+    if (p->tv_lambda > 0) return fail(BSGD_ERR_INVALID_ARG, "serving runs no TV prox");
+    if (p->epochs < 1) return fail(BSGD_ERR_INVALID_ARG, "epochs must be >= 1");
+    if (!(p->alpha > 0 && p->alpha <= 1)) return fail(BSGD_ERR_INVALID_ARG, "alpha in (0, 1]");
+    if (bytes > S->prm.budget_bytes)
+        return fail(BSGD_ERR_BUDGET, "request needs " + std::to_string(bytes) +
+                                         " bytes, more than the server's budget");
+    Request *r = new (std::nothrow) Request();
+    if (!r) return fail(BSGD_ERR_OOM, "host allocation failed");
+    r->desc = *desc;
+    r->angles.assign(desc->angles ? desc->angles : nullptr, desc->angles ? desc->angles + desc->n_views : nullptr);
+    if (desc->view_block) r->view_block.assign(desc->view_block, desc->view_block + desc->n_views);
+    r->desc.angles = desc->angles ? r->angles.data() : nullptr;
+    r->desc.view_block = desc->view_block ? r->view_block.data() : nullptr;
+    r->M = M;
+    r->N = N;
+    r->p = *p;
+    const size_t R = (size_t)desc->n_views * desc->nu * desc->nv;
+    r->y.assign((const char *)y, (const char *)y + R * dtype_size(yt));
+    r->yt = yt;
+    r->x_out = x_out;
+    r->bytes = bytes;
+    const int kM = std::max(1, (int)std::lround(p->alpha * M));
+    const int epoch_len = std::max(1, (int)std::lround(1.0 / (p->alpha * p->gamma)));
+    (void)kM;
+    r->target = (int64_t)p->epochs * epoch_len;
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stopping) {
+            delete r;
+            return fail(BSGD_ERR_STATE, "server is stopping");
+        }
+        r->id = S->next_id++;
+        S->all[r->id] = r;
+        S->queue.push_back(r);
+        S->submitted++;
+        *id = r->id;
+    }
+    S->cv.notify_all();
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_server_poll(bsgd_server *S, int64_t id, int *done) {
+    if (!S || !done) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return fail(BSGD_ERR_INVALID_ARG, "unknown request id");
+    *done = it->second->status == kDone || it->second->status == kFailed;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_server_wait(bsgd_server *S, int64_t id, int timeout_ms, bsgd_report *out) {
+    if (!S) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return fail(BSGD_ERR_INVALID_ARG, "unknown request id");
+    Request *r = it->second;
+    const bool fin = S->cv.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)), [&] {
+        return r->status == kDone || r->status == kFailed;
+    });
+    if (!fin) return fail(BSGD_ERR_TIMEOUT, "request " + std::to_string(id) + " still running");
+    if (r->status == kFailed) return fail(BSGD_ERR_CUDA, "request failed: " + r->error);
+    if (out) *out = r->rep;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_server_get_stats(bsgd_server *S, bsgd_server_stats *out) {
+    if (!S || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    bsgd_server_stats z{};
+    z.submitted = S->submitted;
+    z.admitted = S->admitted;
+    z.completed = S->completed;
+    z.failed = S->failed;
+    z.queued = (int64_t)S->queue.size();
+    z.resident = (int64_t)S->resident.size();
+    z.peak_resident = S->peak_resident;
+    z.bytes_resident = S->bytes;
+    z.peak_bytes = S->peak_bytes;
+    std::vector<double> l = S->latencies_ms;
+    std::sort(l.begin(), l.end());
+    if (!l.empty()) {
+        auto q = [&](double f) { return l[std::min(l.size() - 1, (size_t)std::floor(f * (l.size() - 1) + 0.5))]; };
+        z.p50_ms = q(0.50);
+        z.p99_ms = q(0.99);
+        double s = 0;
+        for (double v : l) s += v;
+        z.mean_ms = s / l.size();
+        z.max_ms = l.back();
+    }
+    z.updates = S->updates;
+    z.busy_s = S->busy_s + (S->busy_since >= 0 ? now_s() - S->busy_since : 0.0);
+    z.rounds = S->rounds;
+    *out = z;
+    return BSGD_OK;
+}

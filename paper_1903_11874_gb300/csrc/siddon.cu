@@ -6,6 +6,8 @@
 // the selected row block(s), z = pair slot (solver). A CTA's rays all belong to
 // one view and one column block, so they share the view's ray table entry and
 // walk a compact bundle of neighbouring voxels.
+#include <algorithm>
+
 #include "siddon_device.cuh"
 
 namespace bsgd {
@@ -65,7 +67,8 @@ __global__ void __launch_bounds__(128) bp_plain_kernel(const DeviceGeom G, const
     });
 }
 
-// Voxel-ray updates (segments longer than 1e-4 of the smallest voxel edge),
+// Voxel-ray updates (segments longer than 1e-4 of the smallest voxel edge;
+// shorter pieces are edge / corner crossings, zero in exact arithmetic),
 // accumulated per (view, cell) into counts.
 template <bool k3D>
 __global__ void __launch_bounds__(128) count_kernel(const DeviceGeom G, const RowSel R, int j0,
@@ -79,8 +82,6 @@ __global__ void __launch_bounds__(128) count_kernel(const DeviceGeom G, const Ro
     RayWalk w;
     unsigned long long c = 0;
     if (ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w)) {
-        // pieces shorter than 1e-4 of the smallest voxel edge are edge / corner
-        // crossings (zero length in exact arithmetic) and are not counted
         const float eps = 1e-4f * fminf(G.hx, fminf(G.hy, G.hz)) / w.L;
         ray_walk(w, [&](int, float s) { c += s > eps ? 1ull : 0ull; });
     }
@@ -109,39 +110,39 @@ __global__ void zero_views_kernel(const DeviceGeom G, const RowSel R, void *y, i
 // ---------------------------------------------------------------------------
 // Solver kernels
 
-template <typename T>
-__device__ __forceinline__ bool solve_pixel(const DeviceGeom &G, const SolveDev &S, int &a, int &i,
-                                            int &j, int &u, int &v, bool &in_band) {
+__device__ __forceinline__ bool solve_pixel(const DeviceGeom &G, const SolveDev &S, int tile,
+                                            int slot, int p, int &a, int &i, int &j, int &u,
+                                            int &v, bool &in_band) {
     const Work &W = *S.work;
-    const int p = blockIdx.z;
     if (p >= W.n_pairs) return false;
     i = W.pair_i[p];
     j = W.pair_j[p];
-    const int slot = blockIdx.y;
     if (slot >= G.block_nviews[i]) return false;
     a = G.block_views[i * G.max_views + slot];
     Band b = G.bands[(size_t)a * (G.N + 1) + j];
     if (S.n_cells > 1) cell_rect(G.nu, G.nv, S.n_cells, S.cells[p * G.max_views + slot], b);
     int nt;
-    in_band = G.nv > 1 ? tile_pixel<true>(b, blockIdx.x, u, v, nt)
-                       : tile_pixel<false>(b, blockIdx.x, u, v, nt);
-    return (int)blockIdx.x < nt;
+    in_band = G.nv > 1 ? tile_pixel<true>(b, tile, u, v, nt) : tile_pixel<false>(b, tile, u, v, nt);
+    return tile < nt;
 }
 
-// FP of the pair's rows: z_new = A_R^J x_J; with FUSED also
-// z^J = z_new, r = y - sum_j z^j and the FP64 row-block residual sums S.
+// FP of the pair's rows for one CTA work item (detector tile, view slot, pair):
+// z_new = A_R^J x_J; with FUSED also z^J = z_new, r = y - sum_j z^j and the FP64
+// row-block residual sums S. The early returns are uniform over the CTA.
 template <typename T, bool FUSED>
-__global__ void __launch_bounds__(128) fp_solve_kernel(const DeviceGeom G, const SolveDev S,
-                                                       const T *__restrict__ x) {
+__device__ __forceinline__ void fp_solve_body(const DeviceGeom &G, const SolveDev &S,
+                                              const T *__restrict__ x, int tile, int slot, int p) {
     int a, i, j, u, v;
     bool act;
-    if (!solve_pixel<T>(G, S, a, i, j, u, v, act)) return;
+    if (!solve_pixel(G, S, tile, slot, p, a, i, j, u, v, act)) return;
     float zn = 0.f;
     if (act) {
+        const bool yf = S.xT != nullptr && G.view_yfast[a];
+        const T *src = yf ? reinterpret_cast<const T *>(S.xT) : x;
         RayWalk w;
-        if (ray_setup(G, a, u, v, G.plane_start[j], G.plane_start[j + 1], w)) {
+        if (ray_setup(G, a, u, v, G.plane_start[j], G.plane_start[j + 1], w, yf)) {
             float acc = 0.f;
-            ray_walk(w, [&](int idx, float s) { acc = fmaf(s, ldf(x + idx), acc); });
+            ray_walk(w, [&](int idx, float s) { acc = fmaf(s, ldf(src + idx), acc); });
             zn = acc * w.L;
         }
     }
@@ -163,20 +164,19 @@ __global__ void __launch_bounds__(128) fp_solve_kernel(const DeviceGeom G, const
         stf(r + row, rn);
         dn = (double)rn * rn - (double)ro * ro;
     }
-    // lanes of one detector row: 8 (3D tile) or 32 (2D tile); the group's first
-    // lane has the lowest u, so it is active whenever any lane of the group is
-    const int group = G.nv > 1 ? 8 : 32;
-    for (int o = group / 2; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
-    if ((threadIdx.x & (group - 1)) == 0 && act && dn != 0.0)
-        atomicAdd(S.S + (size_t)i * G.nv + v, dn);
+    // the 32 lanes of a warp share one detector row; lane 0 has the lowest u,
+    // so it is active whenever any lane of the warp is
+    for (int o = 16; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+    if ((threadIdx.x & 31) == 0 && act && dn != 0.0) atomicAdd(S.S + (size_t)i * G.nv + v, dn);
 }
 
-// BP of the residual change of the pair's rows into g_J; r~^J = r.
+// BP of the residual change of the pair's rows into g_J, and r~^J = r.
 template <typename T>
-__global__ void __launch_bounds__(128) bp_solve_kernel(const DeviceGeom G, const SolveDev S) {
+__device__ __forceinline__ void bp_solve_body(const DeviceGeom &G, const SolveDev &S, int tile,
+                                              int slot, int p) {
     int a, i, j, u, v;
     bool act;
-    if (!solve_pixel<T>(G, S, a, i, j, u, v, act) || !act) return;
+    if (!solve_pixel(G, S, tile, slot, p, a, i, j, u, v, act) || !act) return;
     const int64_t row = ((int64_t)a * G.nv + v) * G.nu + u;
     const T *r = reinterpret_cast<const T *>(S.r);
     T *rt = reinterpret_cast<T *>(S.rt) + (int64_t)j * G.n_rows;
@@ -184,13 +184,94 @@ __global__ void __launch_bounds__(128) bp_solve_kernel(const DeviceGeom G, const
     stf(rt + row, rv);
     const float dw = rv - ro;
     if (dw == 0.f) return;
+    const bool yf = S.gT != nullptr && G.view_yfast[a];
+    float *dst = yf ? S.gT : S.g;
     RayWalk w;
-    if (!ray_setup(G, a, u, v, G.plane_start[j], G.plane_start[j + 1], w)) return;
+    if (!ray_setup(G, a, u, v, G.plane_start[j], G.plane_start[j + 1], w, yf)) return;
     const float wl = dw * w.L;
-    float *gg = S.g;
     ray_walk(w, [&](int idx, float s) {
-        if (s > 0.f) atomicAdd(gg + idx, s * wl);
+        if (s > 0.f) atomicAdd(dst + idx, s * wl);
     });
+}
+
+template <typename T, bool FUSED>
+__global__ void __launch_bounds__(128) fp_solve_kernel(const DeviceGeom G, const SolveDev S,
+                                                       const T *__restrict__ x) {
+    fp_solve_body<T, FUSED>(G, S, x, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) bp_solve_kernel(const DeviceGeom G, const SolveDev S) {
+    bp_solve_body<T>(G, S, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
+// Serving rounds: persistent kernels over the work items of every resident
+// request (one CTA work item = one detector tile of one view of one pair).
+// Items are handed out by an atomic counter, so requests of very different
+// sizes share the GPU without a per-request launch.
+
+__device__ __forceinline__ int round_entry(const ReqDesc *T, int n, long long item) {
+    int r = 0;
+    while (r + 1 < n && T[r + 1].work_begin <= item) ++r;
+    return r;
+}
+
+template <bool kBP>
+__global__ void __launch_bounds__(128) round_solve_kernel(const ReqDesc *__restrict__ T,
+                                                          RoundCtl *__restrict__ C) {
+    __shared__ long long s_item;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = (long long)atomicAdd(kBP ? &C->bp_next : &C->fp_next, 1ull);
+        __syncthreads();
+        const long long item = s_item;
+        __syncthreads();
+        if (item >= C->total_items) return;
+        const ReqDesc &q = T[round_entry(T, C->n, item)];
+        if (!q.active || item >= q.work_begin + q.work_count) continue;
+        long long local = item - q.work_begin;
+        const int tile = (int)(local % q.max_tiles);
+        local /= q.max_tiles;
+        const int slot = (int)(local % q.G.max_views);
+        const int p = (int)(local / q.G.max_views);
+        if (kBP) {
+            if (q.dtype == BSGD_F32) bp_solve_body<float>(q.G, q.S, tile, slot, p);
+            else if (q.dtype == BSGD_BF16) bp_solve_body<__nv_bfloat16>(q.G, q.S, tile, slot, p);
+            else bp_solve_body<__half>(q.G, q.S, tile, slot, p);
+        } else {
+            if (q.dtype == BSGD_F32)
+                fp_solve_body<float, true>(q.G, q.S, (const float *)q.x, tile, slot, p);
+            else if (q.dtype == BSGD_BF16)
+                fp_solve_body<__nv_bfloat16, true>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
+            else
+                fp_solve_body<__half, true>(q.G, q.S, (const __half *)q.x, tile, slot, p);
+        }
+    }
+}
+
+int round_persistent_grid() {
+    int dev = 0, sms = 152, per = 4;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, round_solve_kernel<false>, 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, round_solve_kernel<true>, 128, 0);
+    per = std::max(1, std::min(a, b));
+    cudaGetLastError();
+    return sms * per;
+}
+
+bsgd_status launch_round_fp(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st) {
+    round_solve_kernel<false><<<grid, 128, 0, st>>>(table, ctl);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+bsgd_status launch_round_bp(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st) {
+    round_solve_kernel<true><<<grid, 128, 0, st>>>(table, ctl);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -111,8 +111,10 @@ __device__ __forceinline__ void axis_walk(float q0, float d, float amin, float a
 
 // Set up the walk of the ray of pixel (u, v) at view a through the volume box
 // with the block axis limited to planes [plo, phi). False if the ray misses.
+// With yfast the voxel indices address a copy of the volume stored [z][x][y]
+// (y fastest) instead of [z][y][x].
 __device__ __forceinline__ bool ray_setup(const DeviceGeom &G, int a, int u, int v, int plo,
-                                          int phi, RayWalk &w) {
+                                          int phi, RayWalk &w, bool yfast = false) {
     // ViewRay: p0[3] pu[3] c0[3] cu[3] cv[3] pad; pixel offsets from the detector
     // centre are exact in FP32
     const float4 *p = reinterpret_cast<const float4 *>(G.rays + a);
@@ -152,10 +154,11 @@ __device__ __forceinline__ bool ray_setup(const DeviceGeom &G, int a, int u, int
     if (w.cx == 0) w.tx = kInf;
     if (w.cy == 0) w.ty = kInf;
     if (w.cz == 0) w.tz = kInf;
-    w.sx = d[0] > 0.f ? 1 : -1;
-    w.sy = d[1] > 0.f ? G.nx : -G.nx;
-    w.sz = d[2] > 0.f ? G.nx * G.ny : -(G.nx * G.ny);
-    w.idx = (i0[2] * G.ny + i0[1]) * G.nx + i0[0];
+    const int strx = yfast ? G.ny : 1, stry = yfast ? 1 : G.nx, strz = G.nx * G.ny;
+    w.sx = d[0] > 0.f ? strx : -strx;
+    w.sy = d[1] > 0.f ? stry : -stry;
+    w.sz = d[2] > 0.f ? strz : -strz;
+    w.idx = i0[2] * strz + i0[1] * stry + i0[0] * strx;
     w.n = w.cx + w.cy + w.cz;
     const float lx = d[0] * G.hx, ly = d[1] * G.hy, lz = d[2] * G.hz;
     w.L = sqrtf(fmaf(lx, lx, fmaf(ly, ly, lz * lz)));
@@ -213,8 +216,11 @@ __device__ __forceinline__ Band band_of(const DeviceGeom &G, int a, int j0, int 
 }
 
 // Pixel of this thread inside tile `tile` of band b; false if outside the band.
-// 3D: a CTA of 128 threads covers 16 u x 8 v pixels as 2 x 2 warps of 8 u x 4 v
-// (a compact bundle of rays per warp); 2D: 128 consecutive bins.
+// 3D: a CTA of 128 threads covers 32 u x 4 v pixels, one warp per detector row:
+// the 32 rays of a warp lie side by side across their direction of travel, so
+// at equal steps they touch voxels that are neighbours along one axis (the
+// fast axis of the layout the solver picks for the view). 2D: 128 consecutive
+// bins.
 template <bool kThreeD>
 __device__ __forceinline__ bool tile_pixel(const Band &b, int tile, int &u, int &v, int &ntiles) {
     constexpr int TU = kThreeD ? kTileU3 : kTileU2;
@@ -228,9 +234,8 @@ __device__ __forceinline__ bool tile_pixel(const Band &b, int tile, int &u, int 
     const int tu = tile % ntu, tv = tile / ntu;
     int lu, lv;
     if (kThreeD) {
-        const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        lu = (wid & 1) * 8 + (lane & 7);
-        lv = (wid >> 1) * 4 + (lane >> 3);
+        lu = threadIdx.x & 31;
+        lv = threadIdx.x >> 5;
     } else {
         lu = threadIdx.x;
         lv = 0;

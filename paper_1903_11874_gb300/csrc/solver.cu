@@ -54,38 +54,32 @@ __device__ inline int pick_weighted(double u, const double *w, int n, int stride
     return last;
 }
 
-struct SampleArgs {
-    DeviceGeom G;
-    Work *work;
-    int *cells;                 // kMaxPairs x max_views
-    int64_t *iter;
-    uint64_t seed;
-    int pairs_mode, cells_mode, n_cells, kM, kN;
-    const double *S;            // M x nv
-    const int *wband;           // M x N x 2
-    const double *cw;           // N x n_views x n_cells
-    const int32_t *replay;      // replay_n x stride
-    int64_t replay_start, replay_n;
-    int32_t *trace;             // trace_cap x stride
-    int64_t trace_cap;
-    int stride;
-    const unsigned long long *counts;  // N x n_views x n_cells
-    unsigned long long *updates;
-};
-
 constexpr int kSampleThreads = 128;
 constexpr int kMaxSampleBlocks = 1024;
+constexpr int kSampleSmemS = 2048;     // FP64 residual table entries staged in shared memory
+constexpr int kMaxResidualPairs = 2048;
 
-__global__ void __launch_bounds__(kSampleThreads) sample_kernel(const SampleArgs A) {
-    __shared__ int s_rows[kMaxSampleBlocks], s_cols[kMaxSampleBlocks];
-    __shared__ double s_w[kMaxPairs * 64];
+// One iteration's draw (Algorithm 1's selection step; Algorithm 2's per-view
+// cells), executed by one CTA of kSampleThreads threads. Writes the work list,
+// the chosen cells, the trace entry and the update counter, then advances the
+// iteration counter.
+__device__ void sample_body(const SampleArgs &A) {
+    // one buffer, two uses: the uniform draw's permutations, or the residual
+    // table and the pair weights
+    __shared__ double s_buf[kSampleSmemS + kMaxResidualPairs];
+    int *s_rows = reinterpret_cast<int *>(s_buf);
+    int *s_cols = s_rows + kMaxSampleBlocks;
+    double *s_S = s_buf;
+    double *s_w = s_buf + kSampleSmemS;
     __shared__ int s_np;
     __shared__ int s_pi[kMaxPairs], s_pj[kMaxPairs];
+    __shared__ unsigned long long s_upd;
     const DeviceGeom &G = A.G;
     const int64_t it = *A.iter;
     const int tid = threadIdx.x;
     const bool replay = A.replay && it >= A.replay_start && it - A.replay_start < A.replay_n;
     const int32_t *rep = replay ? A.replay + (it - A.replay_start) * A.stride : nullptr;
+    if (tid == 0) s_upd = 0ull;
 
     if (replay) {
         if (tid == 0) {
@@ -127,11 +121,17 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(const SampleArgs
         }
     } else {  // residual-weighted pair: W_ij = sum_{v in R_ij} S[i][v] + floor
         const int MN = G.M * G.N;
+        const int nS = G.M * G.nv;
+        const bool staged = nS <= kSampleSmemS;
+        if (staged)
+            for (int k = tid; k < nS; k += blockDim.x) s_S[k] = A.S[k];
+        __syncthreads();
+        const double *S = staged ? s_S : A.S;
         for (int k = tid; k < MN; k += blockDim.x) {
             const int i = k / G.N;
             const int lo = A.wband[2 * k], hi = A.wband[2 * k + 1];
             double w = 0.0;
-            for (int v = lo; v <= hi; ++v) w += A.S[(size_t)i * G.nv + v];
+            for (int v = lo; v <= hi; ++v) w += S[(size_t)i * G.nv + v];
             s_w[k] = w;
         }
         __syncthreads();
@@ -148,27 +148,36 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(const SampleArgs
     }
     __syncthreads();
     const int np = s_np;
-    // cells: one per view of each pair's row block
+    // cells: one per view of each pair's row block; voxel-ray updates of the
+    // chosen rows (FP + BP) summed in parallel
+    unsigned long long upd = 0;
     for (int q = tid; q < np * G.max_views; q += blockDim.x) {
         const int p = q / G.max_views, k = q % G.max_views;
         const int i = s_pi[p], j = s_pj[p];
         const int nvb = G.block_nviews[i];
         int c = -1;
-        if (k < nvb && A.cells_mode != BSGD_CELLS_NONE) {
-            if (replay) {
-                c = rep[1 + 2 * np + p * G.max_views + k];
-            } else {
-                const double u = draw_u(A.seed, it, kLaneCells + p * nvb + k);
-                if (A.cells_mode == BSGD_CELLS_UNIFORM) {
-                    c = min((int)(u * A.n_cells), A.n_cells - 1);
+        if (k < nvb) {
+            const int a = G.block_views[i * G.max_views + k];
+            if (A.cells_mode != BSGD_CELLS_NONE) {
+                if (replay) {
+                    c = rep[1 + 2 * np + p * G.max_views + k];
                 } else {
-                    const int a = G.block_views[i * G.max_views + k];
-                    c = pick_weighted(u, A.cw + ((size_t)j * G.n_views + a) * A.n_cells, A.n_cells, 1);
+                    const double u = draw_u(A.seed, it, kLaneCells + p * nvb + k);
+                    if (A.cells_mode == BSGD_CELLS_UNIFORM)
+                        c = min((int)(u * A.n_cells), A.n_cells - 1);
+                    else
+                        c = pick_weighted(u, A.cw + ((size_t)j * G.n_views + a) * A.n_cells,
+                                          A.n_cells, 1);
                 }
             }
+            const unsigned long long *cn = A.counts + ((size_t)j * G.n_views + a) * A.n_cells;
+            if (c >= 0) upd += cn[c];
+            else for (int s = 0; s < A.n_cells; ++s) upd += cn[s];
         }
         A.cells[p * G.max_views + k] = c;
     }
+    for (int o = 16; o > 0; o >>= 1) upd += __shfl_xor_sync(0xffffffffu, upd, o);
+    if ((tid & 31) == 0 && upd) atomicAdd(&s_upd, upd);
     __syncthreads();
     if (tid == 0) {
         Work &W = *A.work;
@@ -186,19 +195,7 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(const SampleArgs
         }
         W.n_cols = nc;
         W.n_rows = nr;
-        // voxel-ray updates of this iteration (FP + BP)
-        unsigned long long upd = 0;
-        for (int p = 0; p < np; ++p) {
-            const int i = s_pi[p], j = s_pj[p];
-            for (int k = 0; k < G.block_nviews[i]; ++k) {
-                const int a = G.block_views[i * G.max_views + k];
-                const unsigned long long *cn = A.counts + ((size_t)j * G.n_views + a) * A.n_cells;
-                const int c = A.cells[p * G.max_views + k];
-                if (c >= 0) upd += cn[c];
-                else for (int s = 0; s < A.n_cells; ++s) upd += cn[s];
-            }
-        }
-        *A.updates += 2ull * upd;
+        *A.updates += 2ull * s_upd;
         if (A.trace && it < A.trace_cap) {
             int32_t *t = A.trace + it * A.stride;
             t[0] = np;
@@ -216,6 +213,8 @@ __global__ void __launch_bounds__(kSampleThreads) sample_kernel(const SampleArgs
     __syncthreads();
     if (tid == 0) *A.iter = it + 1;
 }
+
+__global__ void __launch_bounds__(kSampleThreads) sample_kernel(const SampleArgs A) { sample_body(A); }
 
 // r = y - sum_j z^j over every row of the selected row blocks (used when
 // several column blocks of one row block are selected, so the FPs cannot
@@ -251,26 +250,135 @@ __global__ void residual_kernel(const DeviceGeom G, const SolveDev S) {
 // update works on x + xlo in FP32 and splits the result back, so steps smaller
 // than half an ulp of x still accumulate instead of being rounded away.
 template <typename T>
-__global__ void update_kernel(const DeviceGeom G, const SolveDev S, T *__restrict__ x,
-                              T *__restrict__ xlo) {
+__device__ __forceinline__ float updated(const T *x, const T *xlo, int64_t k, float mu, float g,
+                                         T *xo, T *xloo) {
+    if (xlo == nullptr) {
+        const float nv = fmaf(mu, g, ldv(x + k));
+        stf(xo + k, nv);
+        return rnd(nv, xo);
+    }
+    const float s = fmaf(mu, g, ldv(x + k) + ldv(xlo + k));
+    const float hi = rnd(s, xo);
+    stf(xo + k, hi);
+    stf(xloo + k, s - hi);
+    return hi;
+}
+
+// Work of column block c of the iteration, shared by `nblk` CTAs of 256 threads
+// (this one is `blk`). Without the y-fastest copies: a strided pass over the
+// slab. With them: 32 x 32 (y, x) tiles of each z plane, where the gradient is
+// g + transpose(gT) and the new x is also written transposed into xT, both
+// transposes staged through shared memory so every global access is coalesced.
+template <typename T>
+__device__ void update_body(const DeviceGeom &G, const SolveDev &S, T *__restrict__ x,
+                            T *__restrict__ xlo, int c, int blk, int nblk) {
     const Work &W = *S.work;
-    const int c = blockIdx.y;
     if (c >= W.n_cols) return;
     const int j = W.cols[c];
-    const int64_t b0 = (int64_t)G.plane_start[j] * G.plane_stride;
-    const int64_t b1 = (int64_t)G.plane_start[j + 1] * G.plane_stride;
     const float mu = (float)*S.mu;
-    for (int64_t k = b0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < b1;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        if (xlo == nullptr) {
-            stf(x + k, fmaf(mu, S.g[k], ldv(x + k)));
-        } else {
-            const float s = fmaf(mu, S.g[k], ldv(x + k) + ldv(xlo + k));
-            const float hi = rnd(s, x);
-            stf(x + k, hi);
-            stf(xlo + k, s - hi);
+    if (S.gT == nullptr) {
+        const int64_t b0 = (int64_t)G.plane_start[j] * G.plane_stride;
+        const int64_t b1 = (int64_t)G.plane_start[j + 1] * G.plane_stride;
+        for (int64_t k = b0 + (int64_t)blk * blockDim.x + threadIdx.x; k < b1;
+             k += (int64_t)nblk * blockDim.x)
+            updated(x, xlo, k, mu, S.g[k], x, xlo);
+        return;
+    }
+    __shared__ float sg[32][33];
+    __shared__ float sx[32][33];
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;   // 32 x 8 threads
+    const int tx_n = (G.nx + 31) / 32, ty_n = (G.ny + 31) / 32;
+    const int z0 = G.plane_start[j], nzj = G.plane_start[j + 1] - z0;
+    const int ntiles = tx_n * ty_n * nzj;
+    T *xT = reinterpret_cast<T *>(S.xT);
+    for (int t = blk; t < ntiles; t += nblk) {
+        const int z = z0 + t / (tx_n * ty_n), rem = t % (tx_n * ty_n);
+        const int x0 = (rem % tx_n) * 32, y0 = (rem / tx_n) * 32;
+        __syncthreads();
+        for (int k = row; k < 32; k += 8) {           // gT rows: fixed x, consecutive y
+            const int xx = x0 + k, yy = y0 + lane;
+            sg[k][lane] = (xx < G.nx && yy < G.ny) ? S.gT[((int64_t)z * G.nx + xx) * G.ny + yy] : 0.f;
+        }
+        __syncthreads();
+        for (int k = row; k < 32; k += 8) {           // x rows: fixed y, consecutive x
+            const int yy = y0 + k, xx = x0 + lane;
+            if (xx < G.nx && yy < G.ny) {
+                const int64_t idx = ((int64_t)z * G.ny + yy) * G.nx + xx;
+                sx[k][lane] = updated(x, xlo, idx, mu, S.g[idx] + sg[lane][k], x, xlo);
+            }
+        }
+        __syncthreads();
+        for (int k = row; k < 32; k += 8) {           // xT rows: fixed x, consecutive y
+            const int xx = x0 + k, yy = y0 + lane;
+            if (xx < G.nx && yy < G.ny) stf(xT + ((int64_t)z * G.nx + xx) * G.ny + yy, sx[lane][k]);
         }
     }
+}
+
+// xT = transpose(x) over the whole volume (y fastest), through shared memory.
+template <typename T>
+__global__ void transpose_kernel(const DeviceGeom G, const T *__restrict__ x, T *__restrict__ xT) {
+    __shared__ float sx[32][33];
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int tx_n = (G.nx + 31) / 32, ty_n = (G.ny + 31) / 32;
+    const int ntiles = tx_n * ty_n * G.nz;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int z = t / (tx_n * ty_n), rem = t % (tx_n * ty_n);
+        const int x0 = (rem % tx_n) * 32, y0 = (rem / tx_n) * 32;
+        __syncthreads();
+        for (int k = row; k < 32; k += 8) {
+            const int yy = y0 + k, xx = x0 + lane;
+            if (xx < G.nx && yy < G.ny) sx[k][lane] = ldv(x + ((int64_t)z * G.ny + yy) * G.nx + xx);
+        }
+        __syncthreads();
+        for (int k = row; k < 32; k += 8) {
+            const int xx = x0 + k, yy = y0 + lane;
+            if (xx < G.nx && yy < G.ny) stf(xT + ((int64_t)z * G.nx + xx) * G.ny + yy, sx[lane][k]);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) update_kernel(const DeviceGeom G, const SolveDev S,
+                                                     T *__restrict__ x, T *__restrict__ xlo) {
+    update_body<T>(G, S, x, xlo, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+// Serving rounds: the sampler of every resident request (one CTA each) and the
+// block updates of every resident request (grid rows = table entries).
+__global__ void __launch_bounds__(kSampleThreads) round_sample_kernel(const ReqDesc *__restrict__ T,
+                                                                       const RoundCtl *__restrict__ C) {
+    const int r = blockIdx.x;
+    if (r >= C->n || !T[r].active) return;
+    sample_body(T[r].A);
+}
+
+__global__ void __launch_bounds__(256) round_update_kernel(const ReqDesc *__restrict__ T,
+                                                           const RoundCtl *__restrict__ C) {
+    const int r = blockIdx.y;
+    if (r >= C->n || !T[r].active) return;
+    const ReqDesc &q = T[r];
+    if (q.dtype == BSGD_F32)
+        update_body<float>(q.G, q.S, (float *)q.x, nullptr, 0, blockIdx.x, gridDim.x);
+    else if (q.dtype == BSGD_BF16)
+        update_body<__nv_bfloat16>(q.G, q.S, (__nv_bfloat16 *)q.x, (__nv_bfloat16 *)q.xlo, 0,
+                                   blockIdx.x, gridDim.x);
+    else
+        update_body<__half>(q.G, q.S, (__half *)q.x, (__half *)q.xlo, 0, blockIdx.x, gridDim.x);
+}
+
+bsgd_status launch_round_sample(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
+                                cudaStream_t st) {
+    round_sample_kernel<<<max_slots, kSampleThreads, 0, st>>>(table, ctl);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+bsgd_status launch_round_update(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
+                                cudaStream_t st) {
+    round_update_kernel<<<dim3(152 * 2, max_slots), 256, 0, st>>>(table, ctl);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
 }
 
 // S[block(a)][v] += r^2 over all rows (the FP64 residual table from scratch).
@@ -385,6 +493,8 @@ struct bsgd_state {
     // device memory
     void *y = nullptr, *z = nullptr, *rt = nullptr, *r = nullptr;
     void *xlo = nullptr;        // low-order image term (16-bit storage only)
+    void *xT = nullptr;         // y-fastest copy of x (volumes only)
+    float *gT = nullptr;        // y-fastest part of g (volumes only)
     float *grad = nullptr;
     double *S = nullptr, *cw = nullptr, *d_mu = nullptr;
     Work *work = nullptr;
@@ -434,7 +544,7 @@ static void stage_end(bsgd_state *s, int stage, cudaEvent_t b, int launches, cud
 
 static void free_state(bsgd_state *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
-    void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->grad, s->S, s->cw, s->d_mu, s->work, s->cells,
+    void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->cw, s->d_mu, s->work, s->cells,
                     s->wband, s->d_iter, s->trace, s->replay, s->counts, s->updates};
     for (void *p : ptrs) cudaFree(p);
     delete s;
@@ -571,8 +681,8 @@ static bsgd_status check_params(const bsgd_geometry *g, const bsgd_solve_params 
         return fail(BSGD_ERR_INVALID_ARG, "n_cells must be 4 (3D) or 2 (2D)");
     if (g->M > kMaxSampleBlocks || g->N > kMaxSampleBlocks || g->M > 64)
         return fail(BSGD_ERR_INVALID_ARG, "the solver supports M <= 64 and N <= 1024");
-    if (p->pair_sampling == BSGD_PAIRS_RESIDUAL && g->M * g->N > kMaxPairs * 64)
-        return fail(BSGD_ERR_INVALID_ARG, "residual sampling supports M * N <= 4096");
+    if (p->pair_sampling == BSGD_PAIRS_RESIDUAL && g->M * g->N > kMaxResidualPairs)
+        return fail(BSGD_ERR_INVALID_ARG, "residual sampling supports M * N <= 2048");
     if (p->tv_lambda < 0 || (p->tv_lambda > 0 && p->tv_iters < 1))
         return fail(BSGD_ERR_INVALID_ARG, "tv_lambda >= 0 and tv_iters >= 1");
     return BSGD_OK;
@@ -627,6 +737,8 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         (e = dalloc((void **)&s->counts, 8 * (size_t)N * V * s->n_cells)) ||
         (e = dalloc((void **)&s->updates, 8)) ||
         (s->st != BSGD_F32 && (e = dalloc(&s->xlo, C * es))) ||
+        (g->desc.nz > 1 && (e = dalloc(&s->xT, C * es))) ||
+        (g->desc.nz > 1 && (e = dalloc((void **)&s->gT, C * 4))) ||
         (p->cells == BSGD_CELLS_GEOMETRIC && (e = dalloc((void **)&s->cw, 8 * (size_t)N * V * s->n_cells)))) {
         free_state(s);
         return e;
@@ -638,6 +750,8 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         BSGD_CUDA(cudaMemsetAsync(s->rt, 0, (size_t)N * R * es, st));
         BSGD_CUDA(cudaMemsetAsync(s->grad, 0, C * 4, st));
         if (s->xlo) BSGD_CUDA(cudaMemsetAsync(s->xlo, 0, C * es, st));
+        if (s->xT) BSGD_CUDA(cudaMemsetAsync(s->xT, 0, C * es, st));
+        if (s->gT) BSGD_CUDA(cudaMemsetAsync(s->gT, 0, C * 4, st));
         BSGD_CUDA(cudaMemsetAsync(s->d_iter, 0, 8, st));
         BSGD_CUDA(cudaMemsetAsync(s->updates, 0, 8, st));
         BSGD_CUDA(cudaMemsetAsync(s->counts, 0, 8 * (size_t)N * V * s->n_cells, st));
@@ -721,6 +835,8 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     d.cells = s->cells;
     d.n_cells = s->n_cells;
     d.mu = s->d_mu;
+    d.xT = s->xT;
+    d.gT = s->gT;
     *out = s;
     return BSGD_OK;
 }
@@ -732,9 +848,9 @@ extern "C" bsgd_status bsgd_state_destroy(bsgd_state *s) {
     return BSGD_OK;
 }
 
-static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
+static void fill_sample_args(const bsgd_state *s, SampleArgs &A) {
     const bsgd_geometry *g = s->g;
-    SampleArgs A{};
+    A = SampleArgs{};
     A.G = g->dg;
     A.work = s->work;
     A.cells = s->cells;
@@ -756,6 +872,87 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
     A.stride = s->stride;
     A.counts = s->counts;
     A.updates = s->updates;
+}
+
+namespace bsgd {
+
+bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out) {
+    if (!s || !x || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (!s->fused) return fail(BSGD_ERR_INVALID_ARG, "serving needs one column block per iteration");
+    if (s->p.tv_lambda > 0) return fail(BSGD_ERR_INVALID_ARG, "serving runs no TV prox");
+    const bsgd_geometry *g = s->g;
+    ReqDesc d{};
+    d.G = g->dg;
+    d.S = s->dev;
+    fill_sample_args(s, d.A);
+    d.x = x;
+    d.xlo = s->xlo;
+    d.dtype = s->st;
+    d.max_tiles = std::max(1, s->max_tiles);
+    d.active = s->max_tiles > 0 ? 1 : 0;
+    d.work_count = s->max_tiles > 0 ? (int64_t)s->max_tiles * g->max_views * s->P : 0;
+    int64_t maxJ = 0;
+    for (int j = 0; j < g->N; ++j) maxJ = std::max(maxJ, g->block_cols(j));
+    d.max_block_cols = maxJ;
+    *out = d;
+    return BSGD_OK;
+}
+
+size_t state_bytes(const bsgd_geometry_desc &d, int M, int N, const bsgd_solve_params &p,
+                   size_t *transient) {
+    const size_t R = (size_t)d.n_views * d.nu * d.nv, C = (size_t)d.nx * d.ny * d.nz;
+    const size_t es = dtype_size((bsgd_dtype)p.storage);
+    const int kM = std::max(1, (int)std::lround(p.alpha * M));
+    const int kN = std::max(1, (int)std::lround(p.gamma * N));
+    const int P = kM * kN;
+    int maxV = (d.n_views + M - 1) / M;
+    if (d.view_block) {
+        std::vector<int> cnt(M, 0);
+        for (int a = 0; a < d.n_views; ++a)
+            if (d.view_block[a] >= 0 && d.view_block[a] < M) cnt[d.view_block[a]]++;
+        maxV = *std::max_element(cnt.begin(), cnt.end());
+    }
+    const size_t cells = p.cells == BSGD_CELLS_NONE ? 1 : (size_t)std::max(1, p.n_cells);
+    const size_t stride = 1 + 2 * (size_t)P + (size_t)P * maxV;
+    size_t b = 0;
+    b += R * es * (2 + 2 * (size_t)N);                 // y, r, z^j, r~^j
+    b += C * 4;                                        // g
+    if (es != 4) b += C * es;                          // low-order image term
+    if (d.nz > 1) b += C * (es + 4);                   // y-fastest copies of x and g
+    b += 8 * (size_t)M * d.nv;                         // residual table
+    b += 4 * (size_t)kMaxPairs * maxV + 8 * (size_t)M * N + sizeof(Work) + 64;
+    b += 4 * (size_t)65536 * stride;                   // trace
+    b += 8 * (size_t)N * d.n_views * cells * (p.cells == BSGD_CELLS_GEOMETRIC ? 2 : 1);
+    // geometry tables
+    b += 64 * (size_t)d.n_views + 16 * (size_t)d.n_views * (N + 1) + 4 * ((size_t)M * maxV + M + N + 1 + d.n_views);
+    size_t t = 0;
+    if (p.step_rule != BSGD_STEP_FIXED) t = std::max(t, C * 8 + R * 4 + C * 8 / N + 64);
+    if (p.cells == BSGD_CELLS_GEOMETRIC) t = std::max(t, C * 4 + R * 4);
+    t = std::max(t, 8 * (size_t)d.n_views);
+    if (transient) *transient = t;
+    return b;
+}
+
+}  // namespace bsgd
+
+// xT = transpose(x): the caller's image is the one to trust at the start of
+// every call (and after the TV prox rewrites it).
+static bsgd_status sync_xT(bsgd_state *s, void *x, cudaStream_t st) {
+    if (!s->xT) return BSGD_OK;
+    const bsgd_geometry *g = s->g;
+    const int tiles = ((g->desc.nx + 31) / 32) * ((g->desc.ny + 31) / 32) * g->desc.nz;
+    const int gb = std::max(1, std::min(tiles, 152 * 8));
+    if (s->st == BSGD_F32) transpose_kernel<float><<<gb, 256, 0, st>>>(g->dg, (const float *)x, (float *)s->xT);
+    else if (s->st == BSGD_BF16) transpose_kernel<__nv_bfloat16><<<gb, 256, 0, st>>>(g->dg, (const __nv_bfloat16 *)x, (__nv_bfloat16 *)s->xT);
+    else transpose_kernel<__half><<<gb, 256, 0, st>>>(g->dg, (const __half *)x, (__half *)s->xT);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
+    const bsgd_geometry *g = s->g;
+    SampleArgs A;
+    fill_sample_args(s, A);
     cudaEvent_t b = stage_begin(s, st);
     sample_kernel<<<1, kSampleThreads, 0, st>>>(A);
     BSGD_CUDA(cudaGetLastError());
@@ -779,7 +976,7 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
     }
     int64_t maxJ = 0;
     for (int j = 0; j < g->N; ++j) maxJ = std::max(maxJ, g->block_cols(j));
-    dim3 ug(std::max(1, std::min<int>((int)((maxJ + 255) / 256), 152 * 8)), s->kN);
+    dim3 ug(std::max(1, std::min<int>((int)((maxJ + 1023) / 1024), 152 * 4)), s->kN);
     b = stage_begin(s, st);
     if (s->st == BSGD_F32) update_kernel<float><<<ug, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr);
     else if (s->st == BSGD_BF16) update_kernel<__nv_bfloat16><<<ug, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo);
@@ -790,7 +987,8 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
     if (s->p.tv_lambda > 0 && s->iters % s->epoch_len == 0) {
         b = stage_begin(s, st);
         BSGD_TRY(tv_prox_impl(g, x, s->st, s->mu * s->p.tv_lambda, s->p.tv_iters, st, s->xlo));
-        stage_end(s, BSGD_STAGE_TV, b, 2 * s->p.tv_iters + 2, st);
+        BSGD_TRY(sync_xT(s, x, st));
+        stage_end(s, BSGD_STAGE_TV, b, 2 * s->p.tv_iters + 3, st);
     }
     return BSGD_OK;
 }
@@ -799,6 +997,7 @@ extern "C" bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void
     if (!s || !x) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
     if (n_iters < 0) return fail(BSGD_ERR_INVALID_ARG, "n_iters < 0");
     cudaStream_t st = (cudaStream_t)stream;
+    if (n_iters > 0) BSGD_TRY(sync_xT(s, x, st));
     for (int k = 0; k < n_iters; ++k) BSGD_TRY(one_iteration(s, x, st));
     return BSGD_OK;
 }

@@ -1,0 +1,142 @@
+"""Serving: continuous batching of reconstructions (bsgd_server_*).
+
+CPU: the admission model (bytes a request holds) and the host-side checks.
+GPU: every result equals the same request run alone (and the plain solver),
+requests of mixed geometry, size and storage type overlap on the device,
+admission respects the byte budget and the slot count, and a bounded wait
+returns TIMEOUT without disturbing the request.
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+from paper_1903_11874_gb300 import binding as B
+from paper_1903_11874_gb300 import synth
+
+
+def cone(n, views, nd=None, vox=None):
+    """n^3 volume of (256 / n) mm voxels, views over 360 deg, n x n detector of
+    1.6 * 256 / n mm pixels, DSO 500 / DSD 1000 (the serving workload's shapes)."""
+    nd = nd or n
+    h = 256.0 / n if vox is None else vox
+    return dict(kind="cone3d", nx=n, ny=n, nz=n, dx=h, dy=h, dz=h, n_views=views, nu=nd, nv=nd,
+                du=1.6 * 256.0 / nd, dv=1.6 * 256.0 / nd, dso=500.0, dsd=1000.0)
+
+
+def params(storage=B.F32, seed=1, epochs=2, mu=None):
+    if mu is None:
+        return B.SolveParams(alpha=1 / 4, gamma=1 / 4, epochs=epochs, rho=0.25, power_iters=10,
+                             pair_sampling=B.PAIRS_RESIDUAL, storage=storage, seed=seed)
+    return B.SolveParams(alpha=1 / 4, gamma=1 / 4, epochs=epochs, step_rule=B.STEP_FIXED, mu=mu,
+                         pair_sampling=B.PAIRS_RESIDUAL, storage=storage, seed=seed)
+
+
+# ---- CPU --------------------------------------------------------------------------
+
+def test_request_bytes_model():
+    g = cone(64, 90)
+    f32 = B.bsgd_request_bytes(g, 4, 4, params())
+    bf = B.bsgd_request_bytes(g, 4, 4, params(B.BF16))
+    R = 90 * 64 * 64
+    C = 64 ** 3
+    # the state holds y, r, z^j and r~^j (2 + 2N sinograms) plus the image, g, ...
+    assert f32 >= (2 + 2 * 4) * R * 4 + 3 * C * 4
+    assert bf < f32
+    # growing the problem grows the bill
+    assert B.bsgd_request_bytes(cone(128, 180), 4, 4, params()) > 4 * f32 / 2
+
+
+def test_request_bytes_rejects_bad_geometry():
+    with pytest.raises(B.BSGDError):
+        B.bsgd_request_bytes(dict(cone(64, 90), nx=0), 4, 4, params())
+
+
+# ---- GPU --------------------------------------------------------------------------
+
+def _data(geo, seed):
+    from paper_1903_11874_gb300.binding import Geometry
+    import torch
+    gg = Geometry(M=4, N=4, **geo)
+    n = geo["nx"]
+    vol = synth.ellipsoid_phantom(n, n, n, 6, seed=seed) * 0.01
+    p = torch.zeros(gg.n_rows, device="cuda:0")
+    B.bsgd_forward_project(gg, torch.from_numpy(vol.reshape(-1)).cuda(), p)
+    return p.cpu().numpy().astype(np.float32), gg
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.gpu
+def test_results_alone_equal_results_in_the_mix():
+    """The same request served alone and among other requests of different
+    geometry, size and storage type gives the same image (to float atomics
+    order), and both equal the plain solver."""
+    geoA, geoB, geoC = cone(64, 90), cone(96, 120, nd=80), cone(48, 72)
+    yA, ggA = _data(geoA, 1)
+    yB, _ = _data(geoB, 2)
+    yC, _ = _data(geoC, 3)
+    pA = params(seed=5)
+    srv = B.Server(budget_bytes=8 << 30, max_slots=8)
+    try:
+        ida = srv.submit(geoA, 4, 4, pA, yA)
+        x_alone, rep_alone = srv.wait(ida)
+        # B runs long enough for A and C to be admitted while it is resident
+        ids = [srv.submit(geoB, 4, 4, params(seed=6, epochs=40), yB),
+               srv.submit(geoA, 4, 4, pA, yA),
+               srv.submit(geoC, 4, 4, params(B.BF16, seed=7), yC)]
+        outs = [srv.wait(i) for i in ids]
+        st = srv.stats()
+    finally:
+        srv.close()
+    x_mix = outs[1][0]
+    assert _rel(x_mix, x_alone) <= 1e-5
+    assert outs[1][1]["iteration"] == rep_alone["iteration"] == 2 * 16
+    assert st["completed"] == 4 and st["failed"] == 0
+    assert st["peak_resident"] >= 2          # the requests overlapped on the GPU
+    # the plain one-call solver, same parameters and seed
+    import torch
+    x_plain = np.zeros(ggA.n_cols, dtype=np.float32)
+    B.bsgd_solve(ggA, pA, yA, x_plain)
+    assert _rel(x_alone, x_plain) <= 1e-5
+
+
+@pytest.mark.gpu
+def test_budget_and_slots_bound_admission():
+    geo = cone(64, 90)
+    y, _ = _data(geo, 4)
+    p = params(epochs=3)
+    need = B.bsgd_request_bytes(geo, 4, 4, p)
+    srv = B.Server(budget_bytes=int(2.5 * need), max_slots=8)   # room for two at a time
+    try:
+        ids = [srv.submit(geo, 4, 4, params(epochs=3, seed=s), y) for s in range(5)]
+        for i in ids:
+            srv.wait(i)
+        st = srv.stats()
+        with pytest.raises(B.BSGDError) as ei:
+            srv.submit(cone(128, 180), 4, 4, p, np.zeros(180 * 128 * 128, np.float32))
+        assert ei.value.status == 5                              # over budget
+    finally:
+        srv.close()
+    assert st["completed"] == 5
+    assert st["peak_resident"] <= 2
+    assert st["peak_bytes"] <= int(2.5 * need)
+
+
+@pytest.mark.gpu
+def test_bounded_wait_times_out_and_request_finishes():
+    geo = cone(96, 180)
+    y, _ = _data(geo, 8)
+    srv = B.Server(budget_bytes=8 << 30, max_slots=4)
+    try:
+        rid = srv.submit(geo, 4, 4, params(epochs=6), y)
+        with pytest.raises(B.BSGDError) as ei:
+            srv.wait(rid, timeout_ms=1)
+        assert ei.value.status == 4
+        x, rep = srv.wait(rid)
+        assert rep["iteration"] == 6 * 16 and np.isfinite(x).all() and np.abs(x).max() > 0
+    finally:
+        srv.close()
