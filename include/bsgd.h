@@ -169,6 +169,27 @@ bsgd_status bsgd_count_updates(const bsgd_geometry *g,
                                int64_t *out, void *stream);
 
 /*
+ * bsgd_count_updates without any memory allocation. The paper has no
+ * counterpart: this exists for callers that cannot let a library allocate
+ * device memory (a process whose device memory is owned by a caching or
+ * pre-reserving allocator, a serving loop that must not block on cudaMalloc /
+ * cudaFree, which can synchronise the device). Its per-view counters live in a
+ * fixed __device__ array of 16384 + 1 counters (about 128 KiB, held on every
+ * GPU that loads the library until the process exits).
+ *  - Same arguments, result and threshold as bsgd_count_updates; synchronous.
+ *  - Geometries with more than 16384 views are rejected (INVALID_ARG).
+ *  - Calls no cudaMalloc / cudaFree and no allocating library routine.
+ *  - The first call on a device looks up the array's device address (once per
+ *    device); make that first call before any stream capture.
+ *  - Every call on a device shares the array (each call clears it first);
+ *    calls that overlap on the GPU race and give wrong counts.
+ */
+bsgd_status bsgd_count_updates_noalloc(const bsgd_geometry *g,
+                                       const int32_t *row_blocks, int n_rb,
+                                       const int32_t *col_blocks, int n_cb,
+                                       int64_t *out, void *stream);
+
+/*
  * Step-size estimate lambda_J ~ ||A^J||_2^2 of column block j by power
  * iteration: v0 = 1 / sqrt|J| on J, v <- A^T A v / ||A^T A v|| (iters times),
  * lambda = ||A^J v||^2. Vector state, norms and lambda are FP64 on the device;

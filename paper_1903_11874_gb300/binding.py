@@ -24,7 +24,7 @@ CELLS_NONE, CELLS_GEOMETRIC, CELLS_UNIFORM = 0, 1, 2
 EXPORTS = (
     "bsgd_last_error", "bsgd_status_string", "bsgd_geometry_create", "bsgd_geometry_destroy",
     "bsgd_geometry_get_info", "bsgd_geometry_pair_rays", "bsgd_forward_project", "bsgd_back_project", "bsgd_count_updates",
-    "bsgd_power_iteration", "bsgd_tv_prox", "bsgd_state_create", "bsgd_state_destroy",
+    "bsgd_count_updates_noalloc", "bsgd_power_iteration", "bsgd_tv_prox", "bsgd_state_create", "bsgd_state_destroy",
     "bsgd_block_step", "bsgd_state_query", "bsgd_trace_stride", "bsgd_state_read_trace",
     "bsgd_state_set_replay", "bsgd_state_profile", "bsgd_state_read_profile", "bsgd_solve",
     "bsgd_request_bytes", "bsgd_server_create", "bsgd_server_destroy", "bsgd_server_submit",
@@ -139,6 +139,8 @@ def load(build_if_missing: bool = True):
                                    ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _vp]),
         "bsgd_count_updates": (st, [_vp, _i32p, ctypes.c_int, _i32p, ctypes.c_int,
                                     P(ctypes.c_int64), _vp]),
+        "bsgd_count_updates_noalloc": (st, [_vp, _i32p, ctypes.c_int, _i32p, ctypes.c_int,
+                                            P(ctypes.c_int64), _vp]),
         "bsgd_power_iteration": (st, [_vp, ctypes.c_int, ctypes.c_int, _i32p, ctypes.c_int,
                                       P(ctypes.c_double), _vp]),
         "bsgd_tv_prox": (st, [_vp, _vp, st, ctypes.c_double, ctypes.c_int, _vp]),
@@ -317,6 +319,17 @@ def bsgd_count_updates(geom, row_blocks=None, col_blocks=None, stream=None) -> i
     out = ctypes.c_int64()
     _check(load().bsgd_count_updates(geom.handle, rp, nr, cp, nc, ctypes.byref(out),
                                      _stream(stream)))
+    return int(out.value)
+
+
+def bsgd_count_updates_noalloc(geom, row_blocks=None, col_blocks=None, stream=None) -> int:
+    """bsgd_count_updates for callers that cannot allocate device memory: the
+    library keeps its counters in a fixed device array (at most 16384 views)."""
+    rp, nr, _ra = _ids(row_blocks)
+    cp, nc, _ca = _ids(col_blocks)
+    out = ctypes.c_int64()
+    _check(load().bsgd_count_updates_noalloc(geom.handle, rp, nr, cp, nc, ctypes.byref(out),
+                                             _stream(stream)))
     return int(out.value)
 
 
