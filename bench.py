@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", default="small", choices=["off", "small", "full"])
+    ap.add_argument("--split", action="store_true",
+                    help="run FP and BP as two kernels (to time them apart)")
     return ap.parse_args()
 
 
@@ -148,14 +150,16 @@ def make_inputs(B, gg, torch, dev, seed_offset=0):
 
 
 def algorithmic_bytes(gg, n_pairs_avg_rays, storage_bytes=4):
-    """Compulsory DRAM bytes of one FP and one BP launch (one pair), per the
-    kernels' data flow: FP reads x_J and, per traced ray, y, every z^j and r, and
-    writes z^J and r; BP reads r and r~^J, writes r~^J and read-modify-writes g_J."""
+    """Compulsory DRAM bytes of one pair in the FP, BP and fused FP+BP kernels,
+    per the kernels' data flow: FP reads x_J and, per traced ray, y, every z^j
+    and r, and writes z^J and r; BP reads r and r~^J, writes r~^J and
+    read-modify-writes g_J; the fused kernel does both without re-reading r."""
     vox_j = gg.n_cols // N
     rays = n_pairs_avg_rays
     fp = vox_j * storage_bytes + rays * storage_bytes * (1 + N + 1 + 2)
     bp = rays * storage_bytes * 3 + vox_j * 8
-    return fp, bp
+    fpbp = vox_j * (storage_bytes + 8) + rays * storage_bytes * (N + 6)
+    return {"fp": fp, "bp": bp, "fpbp": fpbp}
 
 
 def run_cuda(args):
@@ -176,6 +180,7 @@ def run_cuda(args):
     prm = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_STRIP, rho=RHO,
                         power_iters=30, pair_sampling=B.PAIRS_RESIDUAL, seed=1 + rank)
     st = B.State(gg, prm, y)
+    st.set_split(args.split)
     mu = st.query()["mu"]
     x = torch.zeros(gg.n_cols, device=dev)
     for _ in range(args.warmup):
@@ -215,15 +220,16 @@ def run_cuda(args):
     # ---- roofline of the dominant kernel (FP or BP), timed live above
     peaks = measured_peaks()
     iters = args.steps * ITERS_PER_EPOCH
-    upd_per_launch = updates / 2.0 / iters            # FP and BP each do half
-    dom = max(("fp", "bp"), key=lambda k: prof[k]["ms"])
+    dom = max(("fp", "bp", "fpbp"), key=lambda k: prof[k]["ms"])
+    # the fused kernel does every update of an iteration; FP and BP half each
+    upd_per_launch = updates / iters / (1.0 if dom == "fpbp" else 2.0)
     launch_ms = prof[dom]["ms"] / max(prof[dom]["launches"], 1)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = 152 * 128 * sm_max * 1e6 / 1e12         # FP32-pipe instr/s, in T/s
     achieved = ALU_OPS_PER_UPDATE * upd_per_launch / (launch_ms * 1e-3) / 1e12
     avg_rays = np.mean([gg.pair_rays(i, j) for i in range(M) for j in range(N)])
-    fpb, bpb = algorithmic_bytes(gg, avg_rays)
-    dom_bytes = fpb if dom == "fp" else bpb
+    # one launch covers the iteration's pairs: (alpha M) x (gamma N) = 1 x 1
+    dom_bytes = algorithmic_bytes(gg, avg_rays)[dom]
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     hbm_ach = dom_bytes / (launch_ms * 1e-3) / 1e9
     roofline = {
@@ -287,6 +293,7 @@ def run_cuda(args):
                        "l2": "inputs larger than L2 (state 1.9 GB; one iteration touches ~150 MB)",
                        "mu": mu, "residual_norm_end": q1["residual_norm"]},
             "gpu_launches": int(launches), "stages_ms": stages,
+            "kernels": "split FP / BP" if args.split else "fused FP+residual+BP",
             "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
             "serving": serving,
         }

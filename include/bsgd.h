@@ -316,7 +316,9 @@ typedef enum {
     BSGD_STAGE_BP = 3,       /* back projection of the residual change        */
     BSGD_STAGE_UPDATE = 4,   /* x_J += mu g_J                                 */
     BSGD_STAGE_TV = 5,       /* TV proximal step (BSGD-TV)                    */
-    BSGD_N_STAGES = 6
+    BSGD_STAGE_FPBP = 6,     /* FP, residual and BP in one kernel (one column
+                                block per iteration)                          */
+    BSGD_N_STAGES = 7
 } bsgd_stage;
 
 typedef struct {
@@ -325,6 +327,9 @@ typedef struct {
 } bsgd_profile;
 
 bsgd_status bsgd_state_profile(bsgd_state *s, int enable);
+/* split = 1: run FP and BP as two kernels even with one column block per
+ * iteration (to time them apart); default 0 (one fused kernel). */
+bsgd_status bsgd_state_set_split(bsgd_state *s, int split);
 bsgd_status bsgd_state_read_profile(bsgd_state *s, bsgd_profile *out, void *stream);
 
 /*

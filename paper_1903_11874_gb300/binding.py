@@ -26,11 +26,12 @@ EXPORTS = (
     "bsgd_geometry_get_info", "bsgd_geometry_pair_rays", "bsgd_forward_project", "bsgd_back_project", "bsgd_count_updates",
     "bsgd_count_updates_noalloc", "bsgd_power_iteration", "bsgd_tv_prox", "bsgd_state_create", "bsgd_state_destroy",
     "bsgd_block_step", "bsgd_state_query", "bsgd_trace_stride", "bsgd_state_read_trace",
-    "bsgd_state_set_replay", "bsgd_state_profile", "bsgd_state_read_profile", "bsgd_solve",
+    "bsgd_state_set_replay", "bsgd_state_profile", "bsgd_state_read_profile",
+    "bsgd_state_set_split", "bsgd_solve",
     "bsgd_request_bytes", "bsgd_server_create", "bsgd_server_destroy", "bsgd_server_submit",
     "bsgd_server_wait", "bsgd_server_poll", "bsgd_server_get_stats",
 )
-STAGES = ("sample", "fp", "residual", "bp", "update", "tv")
+STAGES = ("sample", "fp", "residual", "bp", "update", "tv", "fpbp")
 
 
 class BSGDError(RuntimeError):
@@ -76,7 +77,7 @@ class SolveParamsC(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 6), ("ms", ctypes.c_double * 6)]
+    _fields_ = [("launches", ctypes.c_int64 * 7), ("ms", ctypes.c_double * 7)]
 
 
 class Report(ctypes.Structure):
@@ -152,6 +153,7 @@ def load(build_if_missing: bool = True):
         "bsgd_state_read_trace": (st, [_vp, _i32p, ctypes.c_int64, ctypes.c_int64, _vp]),
         "bsgd_state_set_replay": (st, [_vp, _i32p, ctypes.c_int64]),
         "bsgd_state_profile": (st, [_vp, ctypes.c_int]),
+        "bsgd_state_set_split": (st, [_vp, ctypes.c_int]),
         "bsgd_state_read_profile": (st, [_vp, P(Profile), _vp]),
         "bsgd_solve": (st, [_vp, P(SolveParamsC), _vp, st, _vp, st, P(Report), _vp]),
         "bsgd_request_bytes": (st, [P(GeometryDesc), ctypes.c_int, ctypes.c_int, P(SolveParamsC),
@@ -411,6 +413,9 @@ class State:
 
     def profile(self, enable=True):
         _check(load().bsgd_state_profile(self.handle, int(bool(enable))))
+
+    def set_split(self, split=True):
+        _check(load().bsgd_state_set_split(self.handle, int(bool(split))))
 
     def read_profile(self, stream=None) -> dict:
         pr = Profile()

@@ -203,6 +203,8 @@ bsgd_status launch_fp_solve(const bsgd_geometry *g, const SolveDev &S, const voi
                             cudaStream_t st);
 bsgd_status launch_bp_solve(const bsgd_geometry *g, const SolveDev &S, bsgd_dtype st_t,
                             int max_pairs, int max_tiles, cudaStream_t st);
+bsgd_status launch_fpbp_solve(const bsgd_geometry *g, const SolveDev &S, const void *x,
+                              bsgd_dtype st_t, int max_pairs, int max_tiles, cudaStream_t st);
 bsgd_status launch_count_cells(const bsgd_geometry *g, int j, int n_cells,
                                unsigned long long *d_counts, cudaStream_t st);
 
@@ -248,7 +250,7 @@ struct ReqDesc {
 };
 
 struct RoundCtl {
-    unsigned long long fp_next, bp_next;   // persistent-kernel work counters
+    unsigned long long next;               // persistent-kernel work counter
     int n;                                 // table entries in use
     int pad;
     int64_t total_items;                   // FP / BP work items of the round
@@ -267,8 +269,7 @@ bsgd_status convert(const void *in, bsgd_dtype it, void *out, bsgd_dtype ot, int
 // Round kernels of the server (enqueued once into a captured graph).
 bsgd_status launch_round_sample(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
                                 cudaStream_t st);
-bsgd_status launch_round_fp(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st);
-bsgd_status launch_round_bp(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st);
+bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st);
 bsgd_status launch_round_update(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
                                 cudaStream_t st);
 int round_persistent_grid();

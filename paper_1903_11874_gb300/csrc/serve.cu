@@ -1,15 +1,16 @@
 // Serving: continuous batching of BSGD reconstructions on one GPU.
 //
 // Two host threads drive the GPU:
-//   admission  takes queued requests in arrival order while slots and the
-//              byte budget allow, builds each one's geometry and solver state
-//              (power-iteration step included) on its own stream, and hands
-//              the ready request to the round thread;
+//   admission  (two threads, one stream each) takes queued requests in arrival
+//              order while slots and the byte budget allow, builds each one's
+//              geometry and solver state (power-iteration step, unless a
+//              request with the same geometry and step rule ran before: its
+//              step is reused) and hands the ready request to the round thread;
 //   rounds     keeps a device table of the resident requests and replays one
 //              captured CUDA graph per round: sampler of every request, then
-//              persistent FP and BP kernels that share all requests' detector
-//              tiles through atomic work counters, then every request's block
-//              update. After the last iteration of a request the round thread
+//              one persistent kernel (FP, residual and BP of each ray) that
+//              shares all requests' detector tiles through an atomic work
+//              counter, then every request's block update. After the last iteration of a request the round thread
 //              copies its image out, and once that copy has finished it frees
 //              the request and releases its budget.
 // The graph never changes: the kernels read the table and the number of
@@ -36,6 +37,8 @@ double now_s() {
 }
 
 enum ReqStatus { kQueued, kAdmitting, kReady, kResident, kFinishing, kDone, kFailed };
+
+constexpr int kAdmitThreads = 2;   // requests set up concurrently
 
 struct Request {
     int64_t id = 0;
@@ -75,8 +78,11 @@ struct bsgd_server {
     int admitting = 0;
     size_t bytes = 0, peak_bytes = 0;
     bool stopping = false;
-    std::thread admit_thr, round_thr;
-    cudaStream_t round_stream = nullptr, admit_stream = nullptr;
+    std::vector<std::thread> admit_thr;
+    std::thread round_thr;
+    std::map<std::string, double> mu_cache;  // step size per geometry and step rule
+    cudaStream_t round_stream = nullptr;
+    std::vector<cudaStream_t> admit_streams;
     ReqDesc *d_table = nullptr;
     RoundCtl *d_ctl = nullptr;
     ReqDesc *h_table = nullptr;   // pinned
@@ -110,34 +116,74 @@ void free_request_gpu(Request *r) {
     r->ev = nullptr;
 }
 
-// Build geometry, state and buffers of one request on the admission stream.
-bsgd_status admit_one(bsgd_server *S, Request *r) {
+// Key of the step size: everything the power iteration's result depends on.
+std::string mu_key(const Request *r) {
+    const bsgd_geometry_desc &d = r->desc;
+    std::string k;
+    auto put = [&](const void *p, size_t n) { k.append((const char *)p, n); };
+    put(&d.kind, sizeof d.kind);
+    put(&d.nx, 3 * sizeof(int));
+    put(&d.dx, 3 * sizeof(double));
+    put(&d.n_views, sizeof(int));
+    put(&d.nu, 2 * sizeof(int));
+    put(&d.du, 4 * sizeof(double));
+    if (d.angles) put(d.angles, sizeof(double) * d.n_views);
+    if (d.view_block) put(d.view_block, sizeof(int32_t) * d.n_views);
+    put(&r->M, sizeof(int));
+    put(&r->N, sizeof(int));
+    put(&r->p.step_rule, sizeof(int));
+    put(&r->p.rho, sizeof(double));
+    put(&r->p.power_iters, sizeof(int));
+    return k;
+}
+
+// Build geometry, state and buffers of one request on an admission stream. A
+// request whose geometry and step rule were seen before reuses that step size
+// instead of running the power iteration again.
+bsgd_status admit_one(bsgd_server *S, Request *r, cudaStream_t stream) {
+    const std::string key = r->p.step_rule == BSGD_STEP_FIXED ? std::string() : mu_key(r);
+    bsgd_solve_params prm = r->p;
+    if (!key.empty()) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->mu_cache.find(key);
+        if (it != S->mu_cache.end()) {
+            prm.step_rule = BSGD_STEP_FIXED;
+            prm.mu = it->second;
+        }
+    }
     BSGD_TRY(bsgd_geometry_create(&r->desc, r->M, r->N, &r->g));
     const int64_t R = r->g->n_rows(), C = r->g->n_cols();
     const size_t ys = dtype_size(r->yt), es = dtype_size((bsgd_dtype)r->p.storage);
     void *dy = nullptr;
     BSGD_CUDA(cudaMalloc(&dy, R * ys));
-    cudaError_t e = cudaMemcpyAsync(dy, r->y.data(), R * ys, cudaMemcpyHostToDevice, S->admit_stream);
+    cudaError_t e = cudaMemcpyAsync(dy, r->y.data(), R * ys, cudaMemcpyHostToDevice, stream);
     bsgd_status st = e == cudaSuccess ? BSGD_OK : cuda_fail(e, "copy of y");
-    if (!st) st = bsgd_state_create(r->g, &r->p, dy, r->yt, S->admit_stream, &r->st);
-    cudaStreamSynchronize(S->admit_stream);
+    if (!st) st = bsgd_state_create(r->g, &prm, dy, r->yt, stream, &r->st);
+    cudaStreamSynchronize(stream);
     cudaFree(dy);
     BSGD_TRY(st);
+    if (!key.empty()) {
+        bsgd_report rep{};
+        if (bsgd_state_query(r->st, &rep, stream) == BSGD_OK) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->mu_cache.emplace(key, rep.mu);
+        }
+    }
     r->y.clear();
     r->y.shrink_to_fit();
     BSGD_CUDA(cudaMalloc(&r->x, C * es));
     BSGD_CUDA(cudaMalloc((void **)&r->xf, C * 4));
-    BSGD_CUDA(cudaMemsetAsync(r->x, 0, C * es, S->admit_stream));
+    BSGD_CUDA(cudaMemsetAsync(r->x, 0, C * es, stream));
     BSGD_CUDA(cudaHostAlloc((void **)&r->stage, C * 4, cudaHostAllocDefault));
     BSGD_CUDA(cudaHostAlloc((void **)&r->upd_host, 8, cudaHostAllocDefault));
     BSGD_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
-    BSGD_CUDA(cudaStreamSynchronize(S->admit_stream));
+    BSGD_CUDA(cudaStreamSynchronize(stream));
     ReqDesc tmp;
     BSGD_TRY(state_descriptor(r->st, r->x, &tmp));   // rejects what rounds cannot run
     return BSGD_OK;
 }
 
-void admission_loop(bsgd_server *S) {
+void admission_loop(bsgd_server *S, cudaStream_t stream) {
     cudaSetDevice(S->prm.device);
     for (;;) {
         Request *r = nullptr;
@@ -157,7 +203,7 @@ void admission_loop(bsgd_server *S) {
             S->bytes += r->bytes;
             S->peak_bytes = std::max(S->peak_bytes, S->bytes);
         }
-        bsgd_status st = admit_one(S, r);
+        bsgd_status st = admit_one(S, r, stream);
         std::string err = st ? bsgd_last_error() : "";
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -182,10 +228,9 @@ void admission_loop(bsgd_server *S) {
 bsgd_status build_graph(bsgd_server *S) {
     cudaGraph_t graph = nullptr;
     BSGD_CUDA(cudaStreamBeginCapture(S->round_stream, cudaStreamCaptureModeThreadLocal));
-    cudaMemsetAsync(&S->d_ctl->fp_next, 0, 2 * sizeof(unsigned long long), S->round_stream);
+    cudaMemsetAsync(&S->d_ctl->next, 0, sizeof(unsigned long long), S->round_stream);
     bsgd_status st = launch_round_sample(S->d_table, S->d_ctl, S->prm.max_slots, S->round_stream);
-    if (!st) st = launch_round_fp(S->d_table, S->d_ctl, S->grid, S->round_stream);
-    if (!st) st = launch_round_bp(S->d_table, S->d_ctl, S->grid, S->round_stream);
+    if (!st) st = launch_round_solve(S->d_table, S->d_ctl, S->grid, S->round_stream);
     if (!st) st = launch_round_update(S->d_table, S->d_ctl, S->prm.max_slots, S->round_stream);
     cudaError_t e = cudaStreamEndCapture(S->round_stream, &graph);
     BSGD_TRY(st);
@@ -211,7 +256,7 @@ bsgd_status upload_table(bsgd_server *S) {
     }
     S->h_ctl->n = n;
     S->h_ctl->total_items = begin;
-    S->h_ctl->fp_next = S->h_ctl->bp_next = 0;
+    S->h_ctl->next = 0;
     if (n) BSGD_CUDA(cudaMemcpyAsync(S->d_table, S->h_table, sizeof(ReqDesc) * n,
                                      cudaMemcpyHostToDevice, S->round_stream));
     BSGD_CUDA(cudaMemcpyAsync(S->d_ctl, S->h_ctl, sizeof(RoundCtl), cudaMemcpyHostToDevice,
@@ -357,7 +402,11 @@ extern "C" bsgd_status bsgd_server_create(const bsgd_server_params *p, bsgd_serv
     S->prm = *p;
     auto init = [&]() -> bsgd_status {
         BSGD_CUDA(cudaStreamCreateWithFlags(&S->round_stream, cudaStreamNonBlocking));
-        BSGD_CUDA(cudaStreamCreateWithFlags(&S->admit_stream, cudaStreamNonBlocking));
+        for (int k = 0; k < kAdmitThreads; ++k) {
+            cudaStream_t a = nullptr;
+            BSGD_CUDA(cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+            S->admit_streams.push_back(a);
+        }
         BSGD_CUDA(cudaMalloc((void **)&S->d_table, sizeof(ReqDesc) * p->max_slots));
         BSGD_CUDA(cudaMalloc((void **)&S->d_ctl, sizeof(RoundCtl)));
         BSGD_CUDA(cudaHostAlloc((void **)&S->h_table, sizeof(ReqDesc) * p->max_slots, cudaHostAllocDefault));
@@ -376,11 +425,11 @@ extern "C" bsgd_status bsgd_server_create(const bsgd_server_params *p, bsgd_serv
         if (S->h_table) cudaFreeHost(S->h_table);
         if (S->h_ctl) cudaFreeHost(S->h_ctl);
         if (S->round_stream) cudaStreamDestroy(S->round_stream);
-        if (S->admit_stream) cudaStreamDestroy(S->admit_stream);
+        for (cudaStream_t a : S->admit_streams) cudaStreamDestroy(a);
         delete S;
         return st;
     }
-    S->admit_thr = std::thread(admission_loop, S);
+    for (cudaStream_t a : S->admit_streams) S->admit_thr.emplace_back(admission_loop, S, a);
     S->round_thr = std::thread(round_loop, S);
     *out = S;
     return BSGD_OK;
@@ -398,7 +447,8 @@ extern "C" bsgd_status bsgd_server_destroy(bsgd_server *S) {
         S->queue.clear();
     }
     S->cv.notify_all();
-    if (S->admit_thr.joinable()) S->admit_thr.join();
+    for (auto &t : S->admit_thr)
+        if (t.joinable()) t.join();
     if (S->round_thr.joinable()) S->round_thr.join();
     cudaSetDevice(S->prm.device);
     cudaStreamSynchronize(S->round_stream);
@@ -412,7 +462,7 @@ extern "C" bsgd_status bsgd_server_destroy(bsgd_server *S) {
     cudaFreeHost(S->h_table);
     cudaFreeHost(S->h_ctl);
     cudaStreamDestroy(S->round_stream);
-    cudaStreamDestroy(S->admit_stream);
+    for (cudaStream_t a : S->admit_streams) cudaStreamDestroy(a);
     delete S;
     return BSGD_OK;
 }

@@ -194,6 +194,63 @@ __device__ __forceinline__ void bp_solve_body(const DeviceGeom &G, const SolveDe
     });
 }
 
+// FP, residual and BP of one ray in one pass (one column block per iteration):
+// the ray's BP weight r_new - r~ depends only on its own FP, so the back
+// projection follows the forward walk without waiting for other rays.
+template <typename T>
+__device__ __forceinline__ void fpbp_solve_body(const DeviceGeom &G, const SolveDev &S,
+                                                const T *__restrict__ x, int tile, int slot, int p) {
+    int a, i, j, u, v;
+    bool act;
+    if (!solve_pixel(G, S, tile, slot, p, a, i, j, u, v, act)) return;
+    const int plo = G.plane_start[j], phi = G.plane_start[j + 1];
+    const bool yf = act && S.xT != nullptr && G.view_yfast[a];
+    float zn = 0.f;
+    if (act) {
+        const T *src = yf ? reinterpret_cast<const T *>(S.xT) : x;
+        RayWalk w;
+        if (ray_setup(G, a, u, v, plo, phi, w, yf)) {
+            float acc = 0.f;
+            ray_walk(w, [&](int idx, float s) { acc = fmaf(s, ldf(src + idx), acc); });
+            zn = acc * w.L;
+        }
+    }
+    const int64_t row = act ? ((int64_t)a * G.nv + v) * G.nu + u : 0;
+    T *z = reinterpret_cast<T *>(S.z);
+    double dn = 0.0;
+    float dw = 0.f;
+    if (act) {
+        stf(z + (int64_t)j * G.n_rows + row, zn);
+        zn = rnd(zn, z);
+        float zs = 0.f;
+        for (int jj = 0; jj < G.N; ++jj) zs += jj == j ? zn : ldv(z + (int64_t)jj * G.n_rows + row);
+        T *r = reinterpret_cast<T *>(S.r);
+        T *rt = reinterpret_cast<T *>(S.rt) + (int64_t)j * G.n_rows;
+        const float rn = rnd(ldf(reinterpret_cast<const T *>(S.y) + row) - zs, r);
+        const float ro = ldv(r + row);
+        stf(r + row, rn);
+        dn = (double)rn * rn - (double)ro * ro;
+        dw = rn - ldv(rt + row);
+        stf(rt + row, rn);
+    }
+    for (int o = 16; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+    if ((threadIdx.x & 31) == 0 && act && dn != 0.0) atomicAdd(S.S + (size_t)i * G.nv + v, dn);
+    if (!act || dw == 0.f) return;
+    float *dst = (S.gT != nullptr && G.view_yfast[a]) ? S.gT : S.g;
+    RayWalk w;
+    if (!ray_setup(G, a, u, v, plo, phi, w, S.gT != nullptr && G.view_yfast[a])) return;
+    const float wl = dw * w.L;
+    ray_walk(w, [&](int idx, float s) {
+        if (s > 0.f) atomicAdd(dst + idx, s * wl);
+    });
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) fpbp_solve_kernel(const DeviceGeom G, const SolveDev S,
+                                                         const T *__restrict__ x) {
+    fpbp_solve_body<T>(G, S, x, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 template <typename T, bool FUSED>
 __global__ void __launch_bounds__(128) fp_solve_kernel(const DeviceGeom G, const SolveDev S,
                                                        const T *__restrict__ x) {
@@ -217,13 +274,11 @@ __device__ __forceinline__ int round_entry(const ReqDesc *T, int n, long long it
     return r;
 }
 
-template <bool kBP>
 __global__ void __launch_bounds__(128) round_solve_kernel(const ReqDesc *__restrict__ T,
                                                           RoundCtl *__restrict__ C) {
     __shared__ long long s_item;
     for (;;) {
-        if (threadIdx.x == 0)
-            s_item = (long long)atomicAdd(kBP ? &C->bp_next : &C->fp_next, 1ull);
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&C->next, 1ull);
         __syncthreads();
         const long long item = s_item;
         __syncthreads();
@@ -235,18 +290,12 @@ __global__ void __launch_bounds__(128) round_solve_kernel(const ReqDesc *__restr
         local /= q.max_tiles;
         const int slot = (int)(local % q.G.max_views);
         const int p = (int)(local / q.G.max_views);
-        if (kBP) {
-            if (q.dtype == BSGD_F32) bp_solve_body<float>(q.G, q.S, tile, slot, p);
-            else if (q.dtype == BSGD_BF16) bp_solve_body<__nv_bfloat16>(q.G, q.S, tile, slot, p);
-            else bp_solve_body<__half>(q.G, q.S, tile, slot, p);
-        } else {
-            if (q.dtype == BSGD_F32)
-                fp_solve_body<float, true>(q.G, q.S, (const float *)q.x, tile, slot, p);
-            else if (q.dtype == BSGD_BF16)
-                fp_solve_body<__nv_bfloat16, true>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
-            else
-                fp_solve_body<__half, true>(q.G, q.S, (const __half *)q.x, tile, slot, p);
-        }
+        if (q.dtype == BSGD_F32)
+            fpbp_solve_body<float>(q.G, q.S, (const float *)q.x, tile, slot, p);
+        else if (q.dtype == BSGD_BF16)
+            fpbp_solve_body<__nv_bfloat16>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
+        else
+            fpbp_solve_body<__half>(q.G, q.S, (const __half *)q.x, tile, slot, p);
     }
 }
 
@@ -254,22 +303,15 @@ int round_persistent_grid() {
     int dev = 0, sms = 152, per = 4;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int a = 0, b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, round_solve_kernel<false>, 128, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, round_solve_kernel<true>, 128, 0);
-    per = std::max(1, std::min(a, b));
+    int a = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, round_solve_kernel, 128, 0);
+    per = std::max(1, a);
     cudaGetLastError();
     return sms * per;
 }
 
-bsgd_status launch_round_fp(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st) {
-    round_solve_kernel<false><<<grid, 128, 0, st>>>(table, ctl);
-    BSGD_CUDA(cudaGetLastError());
-    return BSGD_OK;
-}
-
-bsgd_status launch_round_bp(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st) {
-    round_solve_kernel<true><<<grid, 128, 0, st>>>(table, ctl);
+bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st) {
+    round_solve_kernel<<<grid, 128, 0, st>>>(table, ctl);
     BSGD_CUDA(cudaGetLastError());
     return BSGD_OK;
 }
@@ -415,6 +457,16 @@ bsgd_status launch_fp_solve(const bsgd_geometry *g, const SolveDev &S, const voi
     else if (st_t == BSGD_BF16) { FPS_GO(__nv_bfloat16) }
     else { FPS_GO(__half) }
 #undef FPS_GO
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+bsgd_status launch_fpbp_solve(const bsgd_geometry *g, const SolveDev &S, const void *x,
+                              bsgd_dtype st_t, int max_pairs, int max_tiles, cudaStream_t st) {
+    dim3 grid(max_tiles, g->max_views, max_pairs);
+    if (st_t == BSGD_F32) fpbp_solve_kernel<float><<<grid, 128, 0, st>>>(g->dg, S, (const float *)x);
+    else if (st_t == BSGD_BF16) fpbp_solve_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(g->dg, S, (const __nv_bfloat16 *)x);
+    else fpbp_solve_kernel<__half><<<grid, 128, 0, st>>>(g->dg, S, (const __half *)x);
     BSGD_CUDA(cudaGetLastError());
     return BSGD_OK;
 }

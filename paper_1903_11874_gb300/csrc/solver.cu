@@ -506,6 +506,7 @@ struct bsgd_state {
     SolveDev dev{};
     // tracing: event pairs per stage (a pool reused after each read)
     bool profiling = false;
+    bool split = false;          // run FP and BP as separate kernels (profiling aid)
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
@@ -957,7 +958,12 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
     sample_kernel<<<1, kSampleThreads, 0, st>>>(A);
     BSGD_CUDA(cudaGetLastError());
     stage_end(s, BSGD_STAGE_SAMPLE, b, 1, st);
-    if (s->max_tiles > 0) {
+    if (s->max_tiles > 0 && s->fused && !s->split) {
+        // one column block per iteration: FP, residual and BP in one pass
+        b = stage_begin(s, st);
+        BSGD_TRY(launch_fpbp_solve(g, s->dev, x, s->st, s->P, s->max_tiles, st));
+        stage_end(s, BSGD_STAGE_FPBP, b, 1, st);
+    } else if (s->max_tiles > 0) {
         b = stage_begin(s, st);
         BSGD_TRY(launch_fp_solve(g, s->dev, x, s->st, s->P, s->max_tiles, s->fused, st));
         stage_end(s, BSGD_STAGE_FP, b, 1, st);
@@ -1030,6 +1036,12 @@ extern "C" bsgd_status bsgd_state_profile(bsgd_state *s, int enable) {
         s->launches[k] = 0;
         s->ms[k] = 0.0;
     }
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_state_set_split(bsgd_state *s, int split) {
+    if (!s) return fail(BSGD_ERR_INVALID_ARG, "state is NULL");
+    s->split = split != 0;
     return BSGD_OK;
 }
 

@@ -98,6 +98,34 @@ def test_config1_trajectory_matches_oracle():
     assert rel_l2(got, xt) < 0.13       # and it is a reconstruction
 
 
+@pytest.mark.parametrize("name", ["config1", "cone_small"])
+def test_fused_and_split_kernels_agree(name):
+    """With one column block per iteration FP, residual and BP of a ray run in
+    one kernel; the split path (FP kernel, then BP kernel) gives the same
+    iterates, the same residual-driven choices and the same update count, up to
+    the order of the float atomics in g."""
+    s, og, gg, y, mu, _ = problem(name)
+    M, N = s["M"], s["N"]
+    out = []
+    for split in (False, True):
+        prm = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu, seed=4,
+                            pair_sampling=B.PAIRS_RESIDUAL)
+        st = B.State(gg, prm, torch.from_numpy(y.astype(np.float32)).to(DEV))
+        st.set_split(split)
+        x = torch.zeros(gg.n_cols, device=DEV)
+        st.profile(True)
+        st.block_step(x, 24)
+        prof = st.read_profile()
+        out.append((x.cpu().double().numpy(), st.read_trace(24), st.query(), prof))
+    (xf, tf, qf, pf), (xs, ts, qs, ps) = out
+    assert pf["fpbp"]["launches"] == 24 and pf["fp"]["launches"] == 0
+    assert ps["fp"]["launches"] == 24 and ps["bp"]["launches"] == 24 and ps["fpbp"]["launches"] == 0
+    assert rel_l2(xf, xs) <= 1e-5
+    assert np.array_equal(tf, ts)
+    assert qf["updates"] == qs["updates"]
+    assert abs(qf["residual_norm"] - qs["residual_norm"]) <= 1e-5 * qs["residual_norm"]
+
+
 def test_several_column_blocks_per_iteration():
     """alpha = gamma = 1/2 on the paper's 2D set-up: two column blocks share a
     row block, so r is recomputed after both FPs (the unfused path)."""
