@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(128) fp_plain_kernel(const DeviceGeom G, const
     RayWalk w;
     float acc = 0.f;
     if (ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w)) {
-        ray_walk(w, [&](int idx, float s) { acc = fmaf(s, ldf(x + idx), acc); });
+        ray_walk_fast(w, [&](int idx, float s) { acc = fmaf(s, ldf(x + idx), acc); });
         acc *= w.L;
     }
     const int64_t row = ((int64_t)a * G.nv + v) * G.nu + u;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128) bp_plain_kernel(const DeviceGeom G, const
     RayWalk w;
     if (!ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w)) return;
     const float wl = rv * w.L;
-    ray_walk(w, [&](int idx, float s) {
+    ray_walk_fast(w, [&](int idx, float s) {
         if (s > 0.f) atomicAdd(x + idx, s * wl);
     });
 }
@@ -142,7 +142,7 @@ __device__ __forceinline__ void fp_solve_body(const DeviceGeom &G, const SolveDe
         RayWalk w;
         if (ray_setup(G, a, u, v, G.plane_start[j], G.plane_start[j + 1], w, yf)) {
             float acc = 0.f;
-            ray_walk(w, [&](int idx, float s) { acc = fmaf(s, ldf(src + idx), acc); });
+            ray_walk_fast(w, [&](int idx, float s) { acc = fmaf(s, ldf(src + idx), acc); });
             zn = acc * w.L;
         }
     }
@@ -189,7 +189,7 @@ __device__ __forceinline__ void bp_solve_body(const DeviceGeom &G, const SolveDe
     RayWalk w;
     if (!ray_setup(G, a, u, v, G.plane_start[j], G.plane_start[j + 1], w, yf)) return;
     const float wl = dw * w.L;
-    ray_walk(w, [&](int idx, float s) {
+    ray_walk_fast(w, [&](int idx, float s) {
         if (s > 0.f) atomicAdd(dst + idx, s * wl);
     });
 }
@@ -211,7 +211,7 @@ __device__ __forceinline__ void fpbp_solve_body(const DeviceGeom &G, const Solve
         RayWalk w;
         if (ray_setup(G, a, u, v, plo, phi, w, yf)) {
             float acc = 0.f;
-            ray_walk(w, [&](int idx, float s) { acc = fmaf(s, ldf(src + idx), acc); });
+            ray_walk_fast(w, [&](int idx, float s) { acc = fmaf(s, ldf(src + idx), acc); });
             zn = acc * w.L;
         }
     }
@@ -240,7 +240,7 @@ __device__ __forceinline__ void fpbp_solve_body(const DeviceGeom &G, const Solve
     RayWalk w;
     if (!ray_setup(G, a, u, v, plo, phi, w, S.gT != nullptr && G.view_yfast[a])) return;
     const float wl = dw * w.L;
-    ray_walk(w, [&](int idx, float s) {
+    ray_walk_fast(w, [&](int idx, float s) {
         if (s > 0.f) atomicAdd(dst + idx, s * wl);
     });
 }

@@ -54,6 +54,8 @@ struct RayWalk {
     int idx;            // current voxel (flat index in the whole volume)
     int n;              // interior crossings = voxels to visit - 1
     float L;            // |d| in mm: segment length = parameter difference * L
+    float fin;          // parameter from the last interior crossing to the exit face
+    unsigned vmax;      // largest flat voxel index of the volume
 };
 
 // Clip one axis: narrows [amin, amax] and records which axis sets the exit;
@@ -130,9 +132,8 @@ __device__ __forceinline__ bool ray_setup(const DeviceGeom &G, int a, int u, int
         const float q1 = fmaf(fv, r[12 + k], fmaf(fu, r[9 + k], r[6 + k]));
         d[k] = q1 - q0[k];
     }
-    int lo[3] = {0, 0, 0}, hi[3] = {G.nx, G.ny, G.nz};
-    lo[G.axis] = plo;
-    hi[G.axis] = phi;
+    const int lo[3] = {G.axis == 0 ? plo : 0, G.axis == 1 ? plo : 0, G.axis == 2 ? plo : 0};
+    const int hi[3] = {G.axis == 0 ? phi : G.nx, G.axis == 1 ? phi : G.ny, G.axis == 2 ? phi : G.nz};
     float amin = 0.f, amax = 1.f;
     int ex = -1;
     bool ok = true;
@@ -145,6 +146,19 @@ __device__ __forceinline__ bool ray_setup(const DeviceGeom &G, int a, int u, int
     axis_walk(q0[0], d[0], amin, amax, lo[0], hi[0], w.tx, w.Dx, w.cx, i0[0]);
     axis_walk(q0[1], d[1], amin, amax, lo[1], hi[1], w.ty, w.Dy, w.cy, i0[1]);
     axis_walk(q0[2], d[2], amin, amax, lo[2], hi[2], w.tz, w.Dz, w.cz, i0[2]);
+    // parameter of the last interior crossing and of the exit face, each from
+    // the entry in one rounding (plane k of an axis lies at t0 + k D)
+    {
+        float last = 0.f;
+        if (w.cx > 0) last = fmaxf(last, fmaf((float)(w.cx - 1), w.Dx, w.tx));
+        if (w.cy > 0) last = fmaxf(last, fmaf((float)(w.cy - 1), w.Dy, w.ty));
+        if (w.cz > 0) last = fmaxf(last, fmaf((float)(w.cz - 1), w.Dz, w.tz));
+        const float face = ex == 0 ? fmaf((float)w.cx, w.Dx, w.tx)
+                         : ex == 1 ? fmaf((float)w.cy, w.Dy, w.ty)
+                                   : fmaf((float)w.cz, w.Dz, w.tz);
+        w.fin = fmaxf(face - last, 0.f);
+    }
+    w.vmax = (unsigned)(G.nx * G.ny * G.nz - 1);
     // the exit axis's plane after its last interior plane is the exit face
     w.ex = ex;
     w.te = kInf;
@@ -166,7 +180,8 @@ __device__ __forceinline__ bool ray_setup(const DeviceGeom &G, int a, int u, int
 }
 
 // Visit every voxel of the walk: f(voxel, parameter length of the segment).
-// Each step takes the nearest interior plane, subtracts the step from the other
+// This is the exact form, used where segments are counted against a length
+// threshold. Each step takes the nearest interior plane, subtracts the step from the other
 // remaining parameters (small numbers, so little rounding) and resets the
 // crossed axis to exactly one plane spacing. Only axes with interior planes
 // left can step, so the voxel index never leaves the box of entry and exit
@@ -196,6 +211,37 @@ __device__ __forceinline__ void ray_walk(RayWalk &w, F &&f) {
         }
     }
     f(w.idx, w.te < kInf ? fmaxf(w.te, 0.f) : 0.f);
+}
+
+// The same walk for the projector and solver kernels, with about half the
+// instructions per step: no per-axis plane counts (a crossed axis always resets
+// to one plane spacing), a branch-free choice of the crossed axis, and the last
+// segment taken from the set-up (exit face minus last interior crossing).
+// Without the counts an axis whose planes are used up could be chosen again,
+// but only where its next plane (at or beyond the exit) and a pending interior
+// crossing lie within the rounding of the remaining parameters of each other:
+// at the very end of the ray, for a sliver of that rounding's length. Voxel
+// indices are clamped to the volume, so such a sliver can never address memory
+// outside it; FP and BP share this walk, so they stay exact adjoints.
+template <class F>
+__device__ __forceinline__ void ray_walk_fast(const RayWalk &w, F &&f) {
+    float tx = w.tx, ty = w.ty, tz = w.tz;
+    int idx = w.idx;
+#pragma unroll 4
+    for (int t = 0; t < w.n; ++t) {
+        const float s = fminf(tx, fminf(ty, tz));
+        f((int)min((unsigned)idx, w.vmax), s);
+        tx -= s;
+        ty -= s;
+        tz -= s;
+        const bool bx = tx == 0.f;
+        const bool by = !bx && ty == 0.f;
+        idx += bx ? w.sx : (by ? w.sy : w.sz);
+        tx = bx ? w.Dx : tx;
+        ty = by ? w.Dy : ty;
+        tz = (!bx && !by) ? w.Dz : tz;
+    }
+    f((int)min((unsigned)idx, w.vmax), w.fin);
 }
 
 // Band of view a for column blocks [j0, j1) (entry N of the table is the
