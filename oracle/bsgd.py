@@ -13,7 +13,12 @@ Readings of the paper used here (each is also listed in the design doc):
   * sub-detector cells keep SAG memory per cell (snapshot form below), so the
     fixed point stays the least-squares solution of Sec. 4 for any sampling law;
   * residual-weighted pair sampling: p(i, j) ~ sum of r^2 over the detector
-    rows R_ij of J_j's shadow in the views of I_i, plus a small floor.
+    rows R_ij of J_j's shadow in the views of I_i, plus a small floor;
+  * Algorithm 3 counts k in epochs (the paper tests every M epochs); the
+    effective update direction of a window is the sum of the directions g_J
+    the window's updates applied; ||r|| is the maintained ||y - sum_j z^j||;
+    the test starts once three residual checkpoints exist (k >= 2M), and the
+    criterion |theta^e - theta^(e-1)| > t1 is used once two cosines exist.
 """
 import math
 from dataclasses import dataclass, field
@@ -40,6 +45,14 @@ class Params:
     tv_lambda: float = 0.0
     tv_iters: int = 20
     view_block: Optional[np.ndarray] = None
+    # Algorithm 3 (automatic step length): a test every `auto_window` epochs
+    # (0: M epochs, as in the paper)
+    auto_mu: bool = False
+    auto_window: int = 0
+    auto_eps: float = 0.1
+    auto_delta: float = 0.4
+    auto_t1: float = 0.2
+    auto_t2: float = 0.5
 
     @property
     def kM(self) -> int:
@@ -230,6 +243,10 @@ class BSGDState:
         self.cell_w = ([geometric_cell_weights(geom, prm, j) for j in range(prm.N)]
                        if prm.cells == "geometric" else None)
         self.history = []
+        self.mu = prm.mu
+        if prm.auto_mu:
+            self.tuner = AutoMu(prm.auto_window or prm.M, prm.auto_eps, prm.auto_delta,
+                                prm.auto_t1, prm.auto_t2, self.residual_norm(), c_)
 
     def step(self, sel: Optional[Selection] = None):
         geom, prm = self.geom, self.prm
@@ -244,18 +261,72 @@ class BSGDState:
             self.rt[j, R] = self.r[R]
         for j in sorted({j for _, j in sel.pairs}):
             vox = P.column_block_voxels(geom, prm.N, j)
-            self.x[vox] += prm.mu * self.g[vox]
+            self.x[vox] += self.mu * self.g[vox]
+            if prm.auto_mu:
+                self.tuner.eud[vox] += self.g[vox]
         self.it += 1
         if prm.tv_lambda > 0.0 and self.it % prm.epoch_len == 0:   # Algorithm 4
             # Eq. 10 is the TV of a 2D image; volumes use the 3D extension
             shape = geom.vol_shape if geom.nz > 1 else (geom.ny, geom.nx)
-            self.x = tv_prox(self.x.reshape(shape), prm.mu * prm.tv_lambda,
+            self.x = tv_prox(self.x.reshape(shape), self.mu * prm.tv_lambda,
                              prm.tv_iters).reshape(-1)
+        if prm.auto_mu and self.it % (prm.epoch_len * self.tuner.window) == 0:   # Algorithm 3
+            self.mu = self.tuner.test(self.mu, self.residual_norm())
         self.history.append(sel)
         return sel
 
     def residual_norm(self) -> float:
         return float(np.linalg.norm(self.r))
+
+
+class AutoMu:
+    """Algorithm 3. At the end of window e (every `window` epochs) the
+    effective update direction gbar^e (the sum of the directions the window's
+    updates applied) gives theta^e = cos(gbar^e, gbar^(e-1)). With the residual
+    norms rho^e, rho^(e-1), rho^(e-2) at the last three window ends (rho^0 at
+    the start):
+      rho^e < rho^(e-1) < rho^(e-2)                       ->  mu <- (1 + eps) mu
+      rho^e > rho^(e-1) > rho^(e-2) and (theta^e < t2 or
+                            |theta^e - theta^(e-1)| > t1)  ->  mu <- (1 - delta) mu
+    A cosine with a zero direction counts as 1."""
+
+    def __init__(self, window, eps, delta, t1, t2, rho0, n_cols):
+        self.window, self.eps, self.delta, self.t1, self.t2 = window, eps, delta, t1, t2
+        self.rho = [rho0]                 # residual norm at each window end
+        self.theta = []                   # cosine at each window end (None for e = 1)
+        self.eud = np.zeros(n_cols)
+        self.eud_prev = None
+        self.mu_log = []
+
+    @staticmethod
+    def cosine(a, b) -> float:
+        na, nb = float(np.linalg.norm(a)), float(np.linalg.norm(b))
+        return 1.0 if na == 0.0 or nb == 0.0 else float(np.dot(a, b)) / (na * nb)
+
+    def decide(self, mu: float, rho, theta, theta_prev) -> float:
+        """The test of Algorithm 3 on the last three residual norms
+        rho = (rho^(e-2), rho^(e-1), rho^e) and the cosines theta^e and
+        theta^(e-1) (None where not defined yet)."""
+        r2, r1, r0 = rho
+        if r0 < r1 < r2:
+            return mu * (1.0 + self.eps)
+        if r0 > r1 > r2:
+            c2 = theta is not None and theta < self.t2
+            c1 = theta is not None and theta_prev is not None and abs(theta - theta_prev) > self.t1
+            if c1 or c2:
+                return mu * (1.0 - self.delta)
+        return mu
+
+    def test(self, mu: float, rho_now: float) -> float:
+        theta = self.cosine(self.eud, self.eud_prev) if self.eud_prev is not None else None
+        self.rho.append(rho_now)
+        if len(self.rho) >= 3:
+            theta_prev = self.theta[-1] if self.theta else None
+            mu = self.decide(mu, self.rho[-3:], theta, theta_prev)
+        self.theta.append(theta)
+        self.eud_prev, self.eud = self.eud, np.zeros_like(self.eud)
+        self.mu_log.append(mu)
+        return mu
 
 
 def bsgd(geom, y, prm: Params, n_iters: int, x0=None, replay=None):
