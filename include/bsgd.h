@@ -246,6 +246,22 @@ typedef struct {
     int tv_iters;            /* FGP iterations of the prox                          */
     int storage;             /* bsgd_dtype of y, x, z^j, r and snapshots             */
     uint64_t seed;           /* sampling stream (SplitMix64 counter spec)            */
+    /* Algorithm 3 (automatic step length), Sec. 3.5: every auto_window epochs
+     * (0: M epochs) the effective update direction of the window (the sum of
+     * the directions g_J its updates applied) is compared with the previous
+     * one, theta = cosine of the two; with the residual norms ||y - sum_j z^j||
+     * at the last three window ends r0 (oldest), r1, r2:
+     *   r2 < r1 < r0                                     -> mu *= 1 + auto_eps
+     *   r2 > r1 > r0 and (theta < auto_t2 or
+     *        |theta - previous theta| > auto_t1)          -> mu *= 1 - auto_delta
+     * The test runs on the device (no host synchronisation); bsgd_state_query
+     * reports the current mu. Not combined with tv_lambda > 0, nor in served
+     * requests (INVALID_ARG). Memory: two FP64 images. */
+    int auto_mu;             /* 1: on                                                */
+    int auto_window;         /* epochs per test (0: M)                               */
+    double auto_eps;         /* > 0 (the paper's epsilon)                            */
+    double auto_delta;       /* in (0, 1) (the paper's delta; 0.4 in Sec. 5)          */
+    double auto_t1, auto_t2; /* cosine thresholds t_1 > 0, t_2 (Algorithm 3)          */
 } bsgd_solve_params;
 
 typedef struct {

@@ -73,6 +73,8 @@ class SolveParamsC(ctypes.Structure):
         ("power_iters", ctypes.c_int), ("pair_sampling", ctypes.c_int), ("cells", ctypes.c_int),
         ("n_cells", ctypes.c_int), ("tv_lambda", ctypes.c_double), ("tv_iters", ctypes.c_int),
         ("storage", ctypes.c_int), ("seed", ctypes.c_uint64),
+        ("auto_mu", ctypes.c_int), ("auto_window", ctypes.c_int), ("auto_eps", ctypes.c_double),
+        ("auto_delta", ctypes.c_double), ("auto_t1", ctypes.c_double), ("auto_t2", ctypes.c_double),
     ]
 
 
@@ -368,11 +370,21 @@ class SolveParams:
     tv_iters: int = 20
     storage: int = F32
     seed: int = 1
+    # Algorithm 3 (automatic step length); defaults: eps and the cosine
+    # thresholds are readings, delta = 0.4 as in Sec. 5
+    auto_mu: bool = False
+    auto_window: int = 0
+    auto_eps: float = 0.1
+    auto_delta: float = 0.4
+    auto_t1: float = 0.2
+    auto_t2: float = 0.5
 
     def c(self):
         return SolveParamsC(self.alpha, self.gamma, self.epochs, self.step_rule, self.mu, self.rho,
                             self.power_iters, self.pair_sampling, self.cells, self.n_cells,
-                            self.tv_lambda, self.tv_iters, self.storage, self.seed)
+                            self.tv_lambda, self.tv_iters, self.storage, self.seed,
+                            int(bool(self.auto_mu)), self.auto_window, self.auto_eps,
+                            self.auto_delta, self.auto_t1, self.auto_t2)
 
 
 class State:

@@ -184,6 +184,7 @@ struct SolveDev {
     // adjacent addresses
     void *xT;          // image, [z][x][y], storage type
     float *gT;         // their part of the aggregated gradient, [z][x][y]
+    double *eud;       // Algorithm 3: effective update direction of the window (or null)
 };
 
 // Sub-detector cell rectangle (Fig. 2): halves in u for 2 cells, quadrants

@@ -477,6 +477,7 @@ extern "C" bsgd_status bsgd_server_submit(bsgd_server *S, const bsgd_geometry_de
     const int kN = std::max(1, (int)std::lround(p->gamma * N));
     if (kN != 1) return fail(BSGD_ERR_INVALID_ARG, "serving needs gamma * N == 1");
     if (p->tv_lambda > 0) return fail(BSGD_ERR_INVALID_ARG, "serving runs no TV prox");
+    if (p->auto_mu) return fail(BSGD_ERR_INVALID_ARG, "serving runs no automatic step length");
     if (p->epochs < 1) return fail(BSGD_ERR_INVALID_ARG, "epochs must be >= 1");
     if (!(p->alpha > 0 && p->alpha <= 1)) return fail(BSGD_ERR_INVALID_ARG, "alpha in (0, 1]");
     if (bytes > S->prm.budget_bytes)

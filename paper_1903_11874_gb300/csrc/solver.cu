@@ -280,8 +280,11 @@ __device__ void update_body(const DeviceGeom &G, const SolveDev &S, T *__restric
         const int64_t b0 = (int64_t)G.plane_start[j] * G.plane_stride;
         const int64_t b1 = (int64_t)G.plane_start[j + 1] * G.plane_stride;
         for (int64_t k = b0 + (int64_t)blk * blockDim.x + threadIdx.x; k < b1;
-             k += (int64_t)nblk * blockDim.x)
-            updated(x, xlo, k, mu, S.g[k], x, xlo);
+             k += (int64_t)nblk * blockDim.x) {
+            const float gv = S.g[k];
+            updated(x, xlo, k, mu, gv, x, xlo);
+            if (S.eud) S.eud[k] += gv;
+        }
         return;
     }
     __shared__ float sg[32][33];
@@ -304,7 +307,9 @@ __device__ void update_body(const DeviceGeom &G, const SolveDev &S, T *__restric
             const int yy = y0 + k, xx = x0 + lane;
             if (xx < G.nx && yy < G.ny) {
                 const int64_t idx = ((int64_t)z * G.ny + yy) * G.nx + xx;
-                sx[k][lane] = updated(x, xlo, idx, mu, S.g[idx] + sg[lane][k], x, xlo);
+                const float gv = S.g[idx] + sg[lane][k];
+                sx[k][lane] = updated(x, xlo, idx, mu, gv, x, xlo);
+                if (S.eud) S.eud[idx] += gv;
             }
         }
         __syncthreads();
@@ -478,6 +483,110 @@ using namespace bsgd;
 // ---------------------------------------------------------------------------
 // State
 
+// ---------------------------------------------------------------------------
+// Algorithm 3: automatic step length. The update kernel adds every applied
+// direction g_J into eud; at the end of a window the two FP64 reductions below
+// give <eud, eud_prev>, ||eud||^2, ||eud_prev||^2 and ||r||^2 = sum S, and one
+// thread applies the test to mu in device memory.
+
+constexpr int kAutoParts = 608;   // reduction blocks (152 SMs x 4)
+
+struct AutoMuHist {
+    double rho_m1, rho_m2;   // ||r|| at the previous two window ends
+    double theta_m1;         // cosine at the previous window end
+    int have_theta_m1;       // theta_m1 defined
+    int e;                   // windows completed
+};
+
+__device__ inline double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+    return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256) automu_dot_kernel(const double *__restrict__ a,
+                                                         const double *__restrict__ b, int64_t n,
+                                                         double *__restrict__ part) {
+    __shared__ double sh[8];
+    double d = 0.0, na = 0.0, nb = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const double u = a[k], v = b[k];
+        d = fma(u, v, d);
+        na = fma(u, u, na);
+        nb = fma(v, v, nb);
+    }
+    d = block_sum(d, sh);
+    na = block_sum(na, sh);
+    nb = block_sum(nb, sh);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x + 0] = d;
+        part[3 * blockIdx.x + 1] = na;
+        part[3 * blockIdx.x + 2] = nb;
+    }
+}
+
+// ||r|| from the FP64 residual table (sum over row blocks and detector rows)
+__device__ inline double table_norm(const double *S, int nS, double *sh) {
+    double t = 0.0;
+    for (int k = threadIdx.x; k < nS; k += blockDim.x) t += S[k];
+    t = block_sum(t, sh);
+    return sqrt(fmax(t, 0.0));
+}
+
+__global__ void __launch_bounds__(256) automu_init_kernel(const double *S, int nS, AutoMuHist *h) {
+    __shared__ double sh[8];
+    const double rho = table_norm(S, nS, sh);
+    if (threadIdx.x == 0) {
+        h->rho_m1 = rho;
+        h->rho_m2 = 0.0;
+        h->theta_m1 = 0.0;
+        h->have_theta_m1 = 0;
+        h->e = 0;
+    }
+}
+
+__global__ void __launch_bounds__(256) automu_decide_kernel(const double *part, int nparts,
+                                                            const double *S, int nS, AutoMuHist *h,
+                                                            double *mu, double eps, double delta,
+                                                            double t1, double t2) {
+    __shared__ double sh[8];
+    double d = 0.0, na = 0.0, nb = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+        d += part[3 * k];
+        na += part[3 * k + 1];
+        nb += part[3 * k + 2];
+    }
+    d = block_sum(d, sh);
+    na = block_sum(na, sh);
+    nb = block_sum(nb, sh);
+    const double rho = table_norm(S, nS, sh);
+    if (threadIdx.x != 0) return;
+    const int e = ++h->e;
+    const bool have_theta = e >= 2;   // the first window has no previous direction
+    const double theta = !have_theta ? 0.0
+                         : (na == 0.0 || nb == 0.0) ? 1.0 : d / (sqrt(na) * sqrt(nb));
+    if (e >= 2) {
+        const double r0 = h->rho_m2, r1 = h->rho_m1, r2 = rho;
+        if (r2 < r1 && r1 < r0) {
+            *mu *= 1.0 + eps;
+        } else if (r2 > r1 && r1 > r0) {
+            const bool c2 = theta < t2;
+            const bool c1 = h->have_theta_m1 && fabs(theta - h->theta_m1) > t1;
+            if (c1 || c2) *mu *= 1.0 - delta;
+        }
+    }
+    h->rho_m2 = h->rho_m1;
+    h->rho_m1 = rho;
+    h->theta_m1 = theta;
+    h->have_theta_m1 = have_theta;
+}
+
 struct bsgd_state {
     const bsgd_geometry *g = nullptr;
     bsgd_solve_params p{};
@@ -503,6 +612,10 @@ struct bsgd_state {
     int32_t *trace = nullptr, *replay = nullptr;
     int64_t replay_start = 0, replay_n = 0;
     unsigned long long *counts = nullptr, *updates = nullptr;
+    // Algorithm 3
+    int auto_win = 0;            // epochs per test (0: off)
+    double *eud = nullptr, *eud_prev = nullptr, *am_part = nullptr;
+    AutoMuHist *am = nullptr;
     SolveDev dev{};
     // tracing: event pairs per stage (a pool reused after each read)
     bool profiling = false;
@@ -546,7 +659,8 @@ static void stage_end(bsgd_state *s, int stage, cudaEvent_t b, int launches, cud
 static void free_state(bsgd_state *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->cw, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->trace, s->replay, s->counts, s->updates};
+                    s->wband, s->d_iter, s->trace, s->replay, s->counts, s->updates, s->eud,
+                    s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) cudaFree(p);
     delete s;
 }
@@ -686,6 +800,14 @@ static bsgd_status check_params(const bsgd_geometry *g, const bsgd_solve_params 
         return fail(BSGD_ERR_INVALID_ARG, "residual sampling supports M * N <= 2048");
     if (p->tv_lambda < 0 || (p->tv_lambda > 0 && p->tv_iters < 1))
         return fail(BSGD_ERR_INVALID_ARG, "tv_lambda >= 0 and tv_iters >= 1");
+    if (p->auto_mu) {
+        if (!(p->auto_eps > 0) || !(p->auto_delta > 0 && p->auto_delta < 1) || !(p->auto_t1 > 0) ||
+            p->auto_window < 0 || !std::isfinite(p->auto_t2))
+            return fail(BSGD_ERR_INVALID_ARG,
+                        "automatic step: auto_eps > 0, 0 < auto_delta < 1, auto_t1 > 0, auto_window >= 0");
+        if (p->tv_lambda > 0)
+            return fail(BSGD_ERR_INVALID_ARG, "the automatic step is not combined with the TV prox");
+    }
     return BSGD_OK;
 }
 
@@ -740,7 +862,11 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         (s->st != BSGD_F32 && (e = dalloc(&s->xlo, C * es))) ||
         (g->desc.nz > 1 && (e = dalloc(&s->xT, C * es))) ||
         (g->desc.nz > 1 && (e = dalloc((void **)&s->gT, C * 4))) ||
-        (p->cells == BSGD_CELLS_GEOMETRIC && (e = dalloc((void **)&s->cw, 8 * (size_t)N * V * s->n_cells)))) {
+        (p->cells == BSGD_CELLS_GEOMETRIC && (e = dalloc((void **)&s->cw, 8 * (size_t)N * V * s->n_cells))) ||
+        (p->auto_mu && ((e = dalloc((void **)&s->eud, 8 * (size_t)C)) ||
+                        (e = dalloc((void **)&s->eud_prev, 8 * (size_t)C)) ||
+                        (e = dalloc((void **)&s->am_part, 8 * 3 * (size_t)kAutoParts)) ||
+                        (e = dalloc((void **)&s->am, sizeof(AutoMuHist)))))) {
         free_state(s);
         return e;
     }
@@ -813,6 +939,13 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
             s->mu = p->rho / lmax;
         }
         BSGD_CUDA(cudaMemcpyAsync(s->d_mu, &s->mu, 8, cudaMemcpyHostToDevice, st));
+        if (p->auto_mu) {
+            s->auto_win = p->auto_window > 0 ? p->auto_window : M;
+            BSGD_CUDA(cudaMemsetAsync(s->eud, 0, 8 * (size_t)C, st));
+            BSGD_CUDA(cudaMemsetAsync(s->eud_prev, 0, 8 * (size_t)C, st));
+            automu_init_kernel<<<1, 256, 0, st>>>(s->S, M * g->desc.nv, s->am);
+            BSGD_CUDA(cudaGetLastError());
+        }
         BSGD_CUDA(cudaStreamSynchronize(st));
         return BSGD_OK;
     };
@@ -838,6 +971,7 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     d.mu = s->d_mu;
     d.xT = s->xT;
     d.gT = s->gT;
+    d.eud = s->eud;
     *out = s;
     return BSGD_OK;
 }
@@ -990,6 +1124,18 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
     BSGD_CUDA(cudaGetLastError());
     stage_end(s, BSGD_STAGE_UPDATE, b, 1, st);
     s->iters += 1;
+    if (s->auto_win > 0 && s->iters % ((int64_t)s->epoch_len * s->auto_win) == 0) {
+        // end of an Algorithm 3 window: test, then start the next direction
+        const int64_t C = g->n_cols();
+        automu_dot_kernel<<<kAutoParts, 256, 0, st>>>(s->eud, s->eud_prev, C, s->am_part);
+        automu_decide_kernel<<<1, 256, 0, st>>>(s->am_part, kAutoParts, s->S, g->M * g->desc.nv,
+                                                s->am, s->d_mu, s->p.auto_eps, s->p.auto_delta,
+                                                s->p.auto_t1, s->p.auto_t2);
+        BSGD_CUDA(cudaGetLastError());
+        std::swap(s->eud, s->eud_prev);
+        s->dev.eud = s->eud;
+        BSGD_CUDA(cudaMemsetAsync(s->eud, 0, 8 * (size_t)C, st));
+    }
     if (s->p.tv_lambda > 0 && s->iters % s->epoch_len == 0) {
         b = stage_begin(s, st);
         BSGD_TRY(tv_prox_impl(g, x, s->st, s->mu * s->p.tv_lambda, s->p.tv_iters, st, s->xlo));
@@ -1016,11 +1162,13 @@ extern "C" bsgd_status bsgd_state_query(bsgd_state *s, bsgd_report *out, void *s
     unsigned long long upd = 0;
     BSGD_CUDA(cudaMemcpyAsync(S.data(), s->S, 8 * n, cudaMemcpyDeviceToHost, st));
     BSGD_CUDA(cudaMemcpyAsync(&upd, s->updates, 8, cudaMemcpyDeviceToHost, st));
+    double mu = s->mu;
+    BSGD_CUDA(cudaMemcpyAsync(&mu, s->d_mu, 8, cudaMemcpyDeviceToHost, st));
     BSGD_CUDA(cudaStreamSynchronize(st));
     double tot = 0.0;
     for (double v : S) tot += v;
     out->residual_norm = std::sqrt(std::max(tot, 0.0));
-    out->mu = s->mu;
+    out->mu = mu;
     out->iteration = s->iters;
     out->epoch = (double)s->iters / s->epoch_len;
     out->updates = (int64_t)upd;
