@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -96,6 +97,12 @@ struct bsgd_geometry {
     int *d_view_block = nullptr;
     unsigned char *d_view_yfast = nullptr;
     bsgd::DeviceGeom dg{};
+    // Filled on first use by a solver state and kept for the geometry's life
+    // (index: number of detector cells 1, 2 or 4): exact voxel-ray update
+    // counts per (J, view, cell), and the geometric cell weights of Algorithm 2.
+    mutable std::mutex cache_mu;
+    mutable unsigned long long *d_counts[5] = {};
+    mutable double *d_cw[5] = {};
 
     int64_t n_rows() const { return (int64_t)desc.n_views * desc.nv * desc.nu; }
     int64_t n_cols() const { return (int64_t)desc.nx * desc.ny * desc.nz; }

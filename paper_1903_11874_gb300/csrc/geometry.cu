@@ -210,6 +210,10 @@ static void free_geometry(bsgd_geometry *g) {
     cudaFree(g->d_plane_start);
     cudaFree(g->d_view_block);
     cudaFree(g->d_view_yfast);
+    for (int k = 0; k < 5; ++k) {
+        cudaFree(g->d_counts[k]);
+        cudaFree(g->d_cw[k]);
+    }
     delete g;
 }
 

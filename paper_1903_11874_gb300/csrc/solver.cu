@@ -658,8 +658,9 @@ static void stage_end(bsgd_state *s, int stage, cudaEvent_t b, int launches, cud
 
 static void free_state(bsgd_state *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
-    void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->cw, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->trace, s->replay, s->counts, s->updates, s->eud,
+    // counts and cw belong to the geometry's cache
+    void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
+                    s->wband, s->d_iter, s->trace, s->replay, s->updates, s->eud,
                     s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) cudaFree(p);
     delete s;
@@ -816,6 +817,71 @@ bsgd_status tv_prox_impl(const bsgd_geometry *g, void *x, bsgd_dtype xt, double 
                          cudaStream_t st, void *xlo);
 }
 
+// Update counts per (J, view, cell) and, for Algorithm 2, the geometric cell
+// weights w(a, c, J) = 1^T A_(a,c)^J 1 (an FP of J's indicator summed per
+// cell): computed once per geometry and cell count, then shared by every
+// state of the geometry (read-only).
+static bsgd_status geometry_tables(const bsgd_geometry *g, int n_cells, bool weights,
+                                   cudaStream_t st, unsigned long long **counts, double **cw) {
+    std::lock_guard<std::mutex> lock(g->cache_mu);
+    const int N = g->N, M = g->M, V = g->desc.n_views;
+    const int64_t R = g->n_rows(), C = g->n_cols();
+    if (!g->d_counts[n_cells]) {
+        unsigned long long *c = nullptr;
+        BSGD_TRY(dalloc((void **)&c, 8 * (size_t)N * V * n_cells));
+        bsgd_status e = BSGD_OK;
+        if (cudaMemsetAsync(c, 0, 8 * (size_t)N * V * n_cells, st) != cudaSuccess)
+            e = fail(BSGD_ERR_CUDA, "cudaMemsetAsync failed");
+        for (int j = 0; j < N && !e; ++j)
+            e = launch_count_cells(g, j, n_cells, c + (size_t)j * V * n_cells, st);
+        if (!e && cudaStreamSynchronize(st) != cudaSuccess) e = fail(BSGD_ERR_CUDA, "count pass failed");
+        if (e) {
+            cudaStreamSynchronize(st);
+            cudaFree(c);
+            return e;
+        }
+        g->d_counts[n_cells] = c;
+    }
+    *counts = g->d_counts[n_cells];
+    *cw = nullptr;
+    if (!weights) return BSGD_OK;
+    if (!g->d_cw[n_cells]) {
+        double *w = nullptr;
+        float *ind = nullptr, *yj = nullptr;
+        BSGD_TRY(dalloc((void **)&w, 8 * (size_t)N * V * n_cells));
+        bsgd_status e = dalloc((void **)&ind, C * 4);
+        if (!e) e = dalloc((void **)&yj, R * 4);
+        if (!e && cudaMemsetAsync(w, 0, 8 * (size_t)N * V * n_cells, st) != cudaSuccess)
+            e = fail(BSGD_ERR_CUDA, "cudaMemsetAsync failed");
+        std::vector<int> all(M);
+        for (int i = 0; i < M; ++i) all[i] = i;
+        std::vector<float> ones;
+        for (int j = 0; j < N && !e; ++j) {
+            cudaMemsetAsync(ind, 0, C * 4, st);
+            const int64_t b0 = (int64_t)g->plane_start[j] * g->dg.plane_stride;
+            ones.assign(g->block_cols(j), 1.0f);
+            cudaMemcpyAsync(ind + b0, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice, st);
+            cudaStreamSynchronize(st);
+            cudaMemsetAsync(yj, 0, R * 4, st);
+            PlainLaunch L{all.data(), M, j, j + 1, 0};
+            e = launch_fp_plain(g, L, ind, BSGD_F32, yj, BSGD_F32, 1, st);
+            if (!e) cell_sum_kernel<<<grid_for(R), 256, 0, st>>>(g->dg, yj, j, n_cells, w);
+        }
+        if (!e) cell_floor_kernel<<<grid_for((int64_t)N * V), 256, 0, st>>>(g->dg, n_cells, w);
+        if (cudaStreamSynchronize(st) != cudaSuccess && !e) e = fail(BSGD_ERR_CUDA, "cell weights failed");
+        if (!e && cudaGetLastError() != cudaSuccess) e = fail(BSGD_ERR_CUDA, "cell weights failed");
+        cudaFree(ind);
+        cudaFree(yj);
+        if (e) {
+            cudaFree(w);
+            return e;
+        }
+        g->d_cw[n_cells] = w;
+    }
+    *cw = g->d_cw[n_cells];
+    return BSGD_OK;
+}
+
 extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solve_params *p,
                                          const void *y, bsgd_dtype yt, void *stream,
                                          bsgd_state **out) {
@@ -857,12 +923,10 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         (e = dalloc((void **)&s->wband, 4 * g->wband.size())) ||
         (e = dalloc((void **)&s->d_iter, 8)) ||
         (e = dalloc((void **)&s->trace, 4 * (size_t)s->trace_cap * s->stride)) ||
-        (e = dalloc((void **)&s->counts, 8 * (size_t)N * V * s->n_cells)) ||
         (e = dalloc((void **)&s->updates, 8)) ||
         (s->st != BSGD_F32 && (e = dalloc(&s->xlo, C * es))) ||
         (g->desc.nz > 1 && (e = dalloc(&s->xT, C * es))) ||
         (g->desc.nz > 1 && (e = dalloc((void **)&s->gT, C * 4))) ||
-        (p->cells == BSGD_CELLS_GEOMETRIC && (e = dalloc((void **)&s->cw, 8 * (size_t)N * V * s->n_cells))) ||
         (p->auto_mu && ((e = dalloc((void **)&s->eud, 8 * (size_t)C)) ||
                         (e = dalloc((void **)&s->eud_prev, 8 * (size_t)C)) ||
                         (e = dalloc((void **)&s->am_part, 8 * 3 * (size_t)kAutoParts)) ||
@@ -881,42 +945,12 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         if (s->gT) BSGD_CUDA(cudaMemsetAsync(s->gT, 0, C * 4, st));
         BSGD_CUDA(cudaMemsetAsync(s->d_iter, 0, 8, st));
         BSGD_CUDA(cudaMemsetAsync(s->updates, 0, 8, st));
-        BSGD_CUDA(cudaMemsetAsync(s->counts, 0, 8 * (size_t)N * V * s->n_cells, st));
         BSGD_CUDA(cudaMemsetAsync(s->work, 0, sizeof(Work), st));
         BSGD_CUDA(cudaMemsetAsync(s->cells, 0xff, 4 * (size_t)kMaxPairs * g->max_views, st));
         BSGD_CUDA(cudaMemcpyAsync(s->wband, g->wband.data(), 4 * g->wband.size(),
                                   cudaMemcpyHostToDevice, st));
         BSGD_TRY(norm_table(g, s->r, s->st, s->S, st));
-        for (int j = 0; j < N; ++j)
-            BSGD_TRY(launch_count_cells(g, j, s->n_cells, s->counts + (size_t)j * V * s->n_cells, st));
-        if (p->cells == BSGD_CELLS_GEOMETRIC) {
-            // w(a, c, J) = 1^T A_{(a,c)}^J 1: FP of J's indicator, summed per cell
-            float *ind = nullptr, *yj = nullptr;
-            BSGD_TRY(dalloc((void **)&ind, C * 4));
-            bsgd_status e2 = dalloc((void **)&yj, R * 4);
-            if (e2) { cudaFree(ind); return e2; }
-            BSGD_CUDA(cudaMemsetAsync(s->cw, 0, 8 * (size_t)N * V * s->n_cells, st));
-            std::vector<int> all(M);
-            for (int i = 0; i < M; ++i) all[i] = i;
-            std::vector<float> ones;
-            for (int j = 0; j < N && !e2; ++j) {
-                cudaMemsetAsync(ind, 0, C * 4, st);
-                const int64_t b0 = (int64_t)g->plane_start[j] * g->dg.plane_stride;
-                ones.assign(g->block_cols(j), 1.0f);
-                cudaMemcpyAsync(ind + b0, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice, st);
-                cudaStreamSynchronize(st);
-                cudaMemsetAsync(yj, 0, R * 4, st);
-                PlainLaunch L{all.data(), M, j, j + 1, 0};
-                e2 = launch_fp_plain(g, L, ind, BSGD_F32, yj, BSGD_F32, 1, st);
-                if (!e2) cell_sum_kernel<<<grid_for(R), 256, 0, st>>>(g->dg, yj, j, s->n_cells, s->cw);
-            }
-            if (!e2) cell_floor_kernel<<<grid_for((int64_t)N * V), 256, 0, st>>>(g->dg, s->n_cells, s->cw);
-            cudaStreamSynchronize(st);
-            cudaFree(ind);
-            cudaFree(yj);
-            if (e2) return e2;
-            BSGD_CUDA(cudaGetLastError());
-        }
+        BSGD_TRY(geometry_tables(g, s->n_cells, p->cells == BSGD_CELLS_GEOMETRIC, st, &s->counts, &s->cw));
         // step size
         if (p->step_rule == BSGD_STEP_FIXED) {
             s->mu = p->mu;
