@@ -122,28 +122,60 @@ __device__ void sample_body(const SampleArgs &A) {
     } else {  // residual-weighted pair: W_ij = sum_{v in R_ij} S[i][v] + floor
         const int MN = G.M * G.N;
         const int nS = G.M * G.nv;
+        const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
         const bool staged = nS <= kSampleSmemS;
-        if (staged)
+        if (staged) {
+#pragma unroll 4
             for (int k = tid; k < nS; k += blockDim.x) s_S[k] = A.S[k];
+        }
         __syncthreads();
         const double *S = staged ? s_S : A.S;
-        for (int k = tid; k < MN; k += blockDim.x) {
+        // a warp per pair, its lanes over the pair's detector rows (fixed order)
+        for (int k = warp; k < MN; k += nwarps) {
             const int i = k / G.N;
             const int lo = A.wband[2 * k], hi = A.wband[2 * k + 1];
             double w = 0.0;
-            for (int v = lo; v <= hi; ++v) w += S[(size_t)i * G.nv + v];
-            s_w[k] = w;
+            for (int v = lo + lane; v <= hi; v += 32) w += S[(size_t)i * G.nv + v];
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+            if (lane == 0) s_w[k] = w;
         }
         __syncthreads();
-        if (tid == 0) {
-            double tot = 0.0;
-            for (int k = 0; k < MN; ++k) tot += s_w[k];
-            const double fl = kResidualFloor * tot / MN + 1e-300;
-            for (int k = 0; k < MN; ++k) s_w[k] += fl;
-            const int k = pick_weighted(draw_u(A.seed, it, kLanePair), s_w, MN, 1);
-            s_np = 1;
-            s_pi[0] = k / G.N;
-            s_pj[0] = k % G.N;
+        if (warp == 0) {
+            // floor, then the draw: the smallest k whose running sum exceeds
+            // u * total, with the running sums from a warp scan in chunks of 32
+            double t = 0.0;
+            for (int k = lane; k < MN; k += 32) t += s_w[k];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            const double fl = kResidualFloor * t / MN + 1e-300;
+            double carry = 0.0;
+            for (int b = 0; b < MN; b += 32) {            // pass 1: the total
+                double v = b + lane < MN ? s_w[b + lane] + fl : 0.0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double n = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += n;
+                }
+                carry += __shfl_sync(0xffffffffu, v, 31);
+            }
+            const double c = draw_u(A.seed, it, kLanePair) * carry;
+            int pick = -1;
+            carry = 0.0;
+            for (int b = 0; b < MN && pick < 0; b += 32) {   // pass 2: the first crossing
+                double v = b + lane < MN ? s_w[b + lane] + fl : 0.0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double n = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += n;
+                }
+                v += carry;
+                const unsigned hit = __ballot_sync(0xffffffffu, b + lane < MN && v > c);
+                if (hit) pick = b + __ffs(hit) - 1;
+                carry = __shfl_sync(0xffffffffu, v, 31);
+            }
+            if (pick < 0) pick = MN - 1;   // rounding left c at the total: the last pair
+            if (lane == 0) {
+                s_np = 1;
+                s_pi[0] = pick / G.N;
+                s_pj[0] = pick % G.N;
+            }
         }
     }
     __syncthreads();
@@ -1150,7 +1182,11 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
     }
     int64_t maxJ = 0;
     for (int j = 0; j < g->N; ++j) maxJ = std::max(maxJ, g->block_cols(j));
-    dim3 ug(std::max(1, std::min<int>((int)((maxJ + 1023) / 1024), 152 * 4)), s->kN);
+    // with the y-fastest copies: one CTA per 32 x 32 tile of the slab
+    const int64_t nt = s->gT ? ((g->desc.nx + 31) / 32) * (int64_t)((g->desc.ny + 31) / 32) *
+                                   ((maxJ + (int64_t)g->desc.nx * g->desc.ny - 1) / ((int64_t)g->desc.nx * g->desc.ny))
+                             : (maxJ + 1023) / 1024;
+    dim3 ug((unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, 65535)), s->kN);
     b = stage_begin(s, st);
     if (s->st == BSGD_F32) update_kernel<float><<<ug, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr);
     else if (s->st == BSGD_BF16) update_kernel<__nv_bfloat16><<<ug, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo);
