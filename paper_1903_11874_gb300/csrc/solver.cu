@@ -54,7 +54,7 @@ __device__ inline int pick_weighted(double u, const double *w, int n, int stride
     return last;
 }
 
-constexpr int kSampleThreads = 128;
+constexpr int kSampleThreads = 256;
 constexpr int kMaxSampleBlocks = 1024;
 constexpr int kSampleSmemS = 2048;     // FP64 residual table entries staged in shared memory
 constexpr int kMaxResidualPairs = 2048;
@@ -125,19 +125,27 @@ __device__ void sample_body(const SampleArgs &A) {
         const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
         const bool staged = nS <= kSampleSmemS;
         if (staged) {
-#pragma unroll 4
+#pragma unroll 8
             for (int k = tid; k < nS; k += blockDim.x) s_S[k] = A.S[k];
         }
         __syncthreads();
         const double *S = staged ? s_S : A.S;
-        // a warp per pair, its lanes over the pair's detector rows (fixed order)
-        for (int k = warp; k < MN; k += nwarps) {
-            const int i = k / G.N;
-            const int lo = A.wband[2 * k], hi = A.wband[2 * k + 1];
-            double w = 0.0;
-            for (int v = lo + lane; v <= hi; v += 32) w += S[(size_t)i * G.nv + v];
-            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-            if (lane == 0) s_w[k] = w;
+        // a warp per pair, its lanes over the pair's detector rows (fixed
+        // order); a batch of 32 pairs' band limits is fetched in one load per
+        // lane and handed round by shuffles
+        for (int k0 = warp; k0 < MN; k0 += 32 * nwarps) {
+            const int kl = k0 + lane * nwarps;
+            const int lo_l = kl < MN ? A.wband[2 * kl] : 0;
+            const int hi_l = kl < MN ? A.wband[2 * kl + 1] : -1;
+            for (int t = 0; t < 32 && k0 + t * nwarps < MN; ++t) {
+                const int k = k0 + t * nwarps;
+                const int lo = __shfl_sync(0xffffffffu, lo_l, t), hi = __shfl_sync(0xffffffffu, hi_l, t);
+                const int i = k / G.N;
+                double w = 0.0;
+                for (int v = lo + lane; v <= hi; v += 32) w += S[(size_t)i * G.nv + v];
+                for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                if (lane == 0) s_w[k] = w;
+            }
         }
         __syncthreads();
         if (warp == 0) {
@@ -322,32 +330,39 @@ __device__ void update_body(const DeviceGeom &G, const SolveDev &S, T *__restric
     __shared__ float sg[32][33];
     __shared__ float sx[32][33];
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;   // 32 x 8 threads
-    const int tx_n = (G.nx + 31) / 32, ty_n = (G.ny + 31) / 32;
+    const int nx = G.nx, ny = G.ny;
+    const int tx_n = (nx + 31) / 32, ty_n = (ny + 31) / 32;
     const int z0 = G.plane_start[j], nzj = G.plane_start[j + 1] - z0;
     const int ntiles = tx_n * ty_n * nzj;
     T *xT = reinterpret_cast<T *>(S.xT);
     for (int t = blk; t < ntiles; t += nblk) {
         const int z = z0 + t / (tx_n * ty_n), rem = t % (tx_n * ty_n);
         const int x0 = (rem % tx_n) * 32, y0 = (rem / tx_n) * 32;
+        // tile bases: [z][x][y] for gT / xT, [z][y][x] for x, g, xlo, eud
+        const int64_t plane = (int64_t)z * nx * ny;
+        const int64_t bT = plane + (int64_t)x0 * ny + y0;   // + k * ny + lane
+        const int64_t bX = plane + (int64_t)y0 * nx + x0;   // + k * nx + lane
+        const bool full = x0 + 32 <= nx && y0 + 32 <= ny;
         __syncthreads();
+#pragma unroll
         for (int k = row; k < 32; k += 8) {           // gT rows: fixed x, consecutive y
-            const int xx = x0 + k, yy = y0 + lane;
-            sg[k][lane] = (xx < G.nx && yy < G.ny) ? S.gT[((int64_t)z * G.nx + xx) * G.ny + yy] : 0.f;
+            const bool in = full || (x0 + k < nx && y0 + lane < ny);
+            sg[k][lane] = in ? S.gT[bT + k * ny + lane] : 0.f;
         }
         __syncthreads();
+#pragma unroll
         for (int k = row; k < 32; k += 8) {           // x rows: fixed y, consecutive x
-            const int yy = y0 + k, xx = x0 + lane;
-            if (xx < G.nx && yy < G.ny) {
-                const int64_t idx = ((int64_t)z * G.ny + yy) * G.nx + xx;
+            if (full || (y0 + k < ny && x0 + lane < nx)) {
+                const int64_t idx = bX + k * nx + lane;
                 const float gv = S.g[idx] + sg[lane][k];
                 sx[k][lane] = updated(x, xlo, idx, mu, gv, x, xlo);
                 if (S.eud) S.eud[idx] += gv;
             }
         }
         __syncthreads();
+#pragma unroll
         for (int k = row; k < 32; k += 8) {           // xT rows: fixed x, consecutive y
-            const int xx = x0 + k, yy = y0 + lane;
-            if (xx < G.nx && yy < G.ny) stf(xT + ((int64_t)z * G.nx + xx) * G.ny + yy, sx[lane][k]);
+            if (full || (x0 + k < nx && y0 + lane < ny)) stf(xT + bT + k * ny + lane, sx[lane][k]);
         }
     }
 }
