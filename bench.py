@@ -55,6 +55,28 @@ SERVE_FULL = dict(n_req=200, sizes=(64, 128, 256, 384), views=(90, 180, 360, 720
 SERVE_SMALL = dict(n_req=16, sizes=(64, 128, 256), views=(90, 180, 360), epochs=2)
 
 
+# Paper-scale 3D workload (Sec. 5, Table 1): source 1536 mm from the rotation
+# centre, detector 1000 mm behind it (DSD 2536), a 400 mm square detector, a
+# 256 mm cube, 360 views at 1 deg; M = 5 view groups (a seeded random partition
+# into equal groups, as in Sec. 5), N = 8 column blocks, alpha = 1/5,
+# gamma = 2/8 (two column blocks per iteration). Noise-free projections, as in
+# the paper's FP / BP timing runs.
+PAPER_CASES = {"case1": (256, 400), "case2": (512, 1000)}
+
+
+def paper_geom(n, nd):
+    h, p = 256.0 / n, 400.0 / nd
+    return dict(kind="cone3d", nx=n, ny=n, nz=n, dx=h, dy=h, dz=h, n_views=360, nu=nd, nv=nd,
+                du=p, dv=p, dso=1536.0, dsd=2536.0)
+
+
+def paper_partition(seed=5):
+    import numpy as np
+    vb = np.repeat(np.arange(5, dtype=np.int32), 72)
+    np.random.default_rng(seed).shuffle(vb)
+    return vb
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -66,6 +88,8 @@ def parse():
     ap.add_argument("--serving", default="small", choices=["off", "small", "full"])
     ap.add_argument("--split", action="store_true",
                     help="run FP and BP as two kernels (to time them apart)")
+    ap.add_argument("--paper-scale", default="case1,case2",
+                    help="paper-scale cases to time (comma list of case1, case2; 'off')")
     return ap.parse_args()
 
 
@@ -272,6 +296,10 @@ def run_cuda(args):
                "h2d_bytes_per_step": int(gg.n_rows * 4), "d2h_bytes_per_step": int(gg.n_cols * 4),
                "api": "bsgd_solve (1 epoch per call, pinned host y and x, fixed mu)"}
 
+    paper = None
+    if args.paper_scale != "off" and rank == 0 and world == 1:
+        paper = paper_scale_leg(B, torch, dev, [c for c in args.paper_scale.split(",") if c])
+
     serving = None
     if args.serving != "off":
         serving = serving_leg(B, torch, dev, SERVE_FULL if args.serving == "full" else SERVE_SMALL,
@@ -295,7 +323,7 @@ def run_cuda(args):
             "gpu_launches": int(launches), "stages_ms": stages,
             "kernels": "split FP / BP" if args.split else "fused FP+residual+BP",
             "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "serving": serving,
+            "serving": serving, "paper_scale": paper,
         }
         print(json.dumps(line))
     if world > 1:
@@ -310,6 +338,61 @@ def serve_geometry(n, views):
     h = 256.0 / n
     return dict(kind="cone3d", nx=n, ny=n, nz=n, dx=h, dy=h, dz=h, n_views=views, nu=n, nv=n,
                 du=1.6 * h, dv=1.6 * h, dso=500.0, dsd=1000.0)
+
+
+def paper_scale_leg(B, torch, dev, cases, warm=2, iters=10):
+    """FP and BP time per BSGD iteration on the paper's Table 1 cases (the
+    analogue of Sec. 5's per-iteration FP / BP timing), one GPU."""
+    import numpy as np
+    from paper_1903_11874_gb300 import synth
+    out = {}
+    for name in cases:
+        n, nd = PAPER_CASES[name]
+        geo = paper_geom(n, nd)
+        gg = B.Geometry(M=5, N=8, view_block=paper_partition(), **geo)
+        base = synth.ellipsoid_phantom(256, 256, 256, 10, seed=0) * KAPPA
+        vol = torch.from_numpy(base).to(dev)
+        if n != 256:   # the same phantom at the finer grid (nearest neighbour)
+            f = n // 256
+            vol = vol.repeat_interleave(f, 0).repeat_interleave(f, 1).repeat_interleave(f, 2)
+        y = torch.zeros(gg.n_rows, device=dev)
+        B.bsgd_forward_project(gg, vol.reshape(-1).contiguous(), y)
+        del vol
+        prm = B.SolveParams(alpha=1 / 5, gamma=2 / 8, step_rule=B.STEP_STRIP, rho=RHO, power_iters=5,
+                            pair_sampling=B.PAIRS_UNIFORM, seed=1)
+        t0 = time.perf_counter()
+        st = B.State(gg, prm, y)
+        t_setup = time.perf_counter() - t0
+        x = torch.zeros(gg.n_cols, device=dev)
+        st.block_step(x, warm)
+        torch.cuda.synchronize()
+        q0 = st.query()
+        st.profile(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st.block_step(x, iters)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / iters
+        prof = st.read_profile()
+        q1 = st.query()
+        upd = (q1["updates"] - q0["updates"]) / iters
+        out[name] = {
+            "volume": "%d^3 (%.2f mm)" % (n, 256.0 / n), "detector": "%d^2 (%.2f mm)" % (nd, 400.0 / nd),
+            "rows": gg.n_rows, "cols": gg.n_cols, "blocks": "M=5 (random partition), N=8 z-slabs, "
+            "alpha=1/5, gamma=2/8",
+            "ms_per_iteration": round(ms, 3),
+            "fp_ms_per_iteration": round(prof["fp"]["ms"] / iters, 3),
+            "residual_ms_per_iteration": round(prof["residual"]["ms"] / iters, 3),
+            "bp_ms_per_iteration": round(prof["bp"]["ms"] / iters, 3),
+            "updates_per_iteration": int(upd),
+            "value": round(upd / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+            "state_setup_s": round(t_setup, 2),
+        }
+        st.close()
+        del y, x
+        torch.cuda.empty_cache()
+    return out
 
 
 def serving_leg(B, torch, dev, cfg, seed=3, rate=20.0, budget=160 << 30):

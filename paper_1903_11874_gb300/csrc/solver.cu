@@ -256,11 +256,16 @@ __device__ void sample_body(const SampleArgs &A) {
 
 __global__ void __launch_bounds__(kSampleThreads) sample_kernel(const SampleArgs A) { sample_body(A); }
 
-// r = y - sum_j z^j over every row of the selected row blocks (used when
-// several column blocks of one row block are selected, so the FPs cannot
-// update r themselves), with the FP64 row-block residual sums.
+// r = y - sum_j z^j over the rows of the selected row blocks that the
+// iteration's FPs changed (the union of the selected column blocks' bands in
+// each view), used when several column blocks of one row block are selected
+// so the FPs cannot update r themselves; with the FP64 row-block residual sums,
+// reduced over the CTA into one atomic per detector row. A CTA covers
+// kResRows detector rows of one view.
+constexpr int kResRows = 4;
+
 template <typename T>
-__global__ void residual_kernel(const DeviceGeom G, const SolveDev S) {
+__global__ void __launch_bounds__(256) residual_kernel(const DeviceGeom G, const SolveDev S) {
     const Work &W = *S.work;
     const int rb = blockIdx.z;
     if (rb >= W.n_rows) return;
@@ -268,19 +273,43 @@ __global__ void residual_kernel(const DeviceGeom G, const SolveDev S) {
     const int slot = blockIdx.y;
     if (slot >= G.block_nviews[i]) return;
     const int a = G.block_views[i * G.max_views + slot];
-    const int per = G.nv * G.nu;
+    Band b{1 << 30, -1, 1 << 30, -1};
+    for (int c = 0; c < W.n_cols; ++c) {
+        const Band q = G.bands[(size_t)a * (G.N + 1) + W.cols[c]];
+        if (q.u0 > q.u1 || q.v0 > q.v1) continue;
+        b.u0 = min(b.u0, q.u0);
+        b.u1 = max(b.u1, q.u1);
+        b.v0 = min(b.v0, q.v0);
+        b.v1 = max(b.v1, q.v1);
+    }
+    const int vbeg = b.v0 + blockIdx.x * kResRows;
+    if (b.u0 > b.u1 || vbeg > b.v1) return;
     const T *y = reinterpret_cast<const T *>(S.y);
     const T *z = reinterpret_cast<const T *>(S.z);
     T *r = reinterpret_cast<T *>(S.r);
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < per; k += gridDim.x * blockDim.x) {
-        const int64_t row = (int64_t)a * per + k;
-        float zs = 0.f;
-        for (int jj = 0; jj < G.N; ++jj) zs += ldv(z + (int64_t)jj * G.n_rows + row);
-        const float rn = rnd(ldf(y + row) - zs, r);
-        const float ro = ldv(r + row);
-        if (rn != ro) {
-            stf(r + row, rn);
-            atomicAdd(S.S + (size_t)i * G.nv + k / G.nu, (double)rn * rn - (double)ro * ro);
+    __shared__ double sh[8];
+    for (int v = vbeg; v < vbeg + kResRows && v <= b.v1; ++v) {
+        const int64_t base = ((int64_t)a * G.nv + v) * G.nu;
+        double dn = 0.0;
+        for (int u = b.u0 + threadIdx.x; u <= b.u1; u += blockDim.x) {
+            const int64_t row = base + u;
+            float zs = 0.f;
+            for (int jj = 0; jj < G.N; ++jj) zs += ldv(z + (int64_t)jj * G.n_rows + row);
+            const float rn = rnd(ldf(y + row) - zs, r);
+            const float ro = ldv(r + row);
+            if (rn != ro) {
+                stf(r + row, rn);
+                dn += (double)rn * rn - (double)ro * ro;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dn;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+            if (t != 0.0) atomicAdd(S.S + (size_t)i * G.nv + v, t);
         }
     }
 }
@@ -1184,7 +1213,7 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
         stage_end(s, BSGD_STAGE_FP, b, 1, st);
         if (!s->fused) {
             b = stage_begin(s, st);
-            dim3 grid(std::max(1, std::min(64, (g->desc.nu * g->desc.nv + 255) / 256)), g->max_views, s->kM);
+            dim3 grid((g->desc.nv + kResRows - 1) / kResRows, g->max_views, s->kM);
             if (s->st == BSGD_F32) residual_kernel<float><<<grid, 256, 0, st>>>(g->dg, s->dev);
             else if (s->st == BSGD_BF16) residual_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(g->dg, s->dev);
             else residual_kernel<__half><<<grid, 256, 0, st>>>(g->dg, s->dev);

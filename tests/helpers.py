@@ -17,10 +17,23 @@ SPECS = {
     "cone_small": dict(kind="cone3d", nx=40, ny=36, nz=32, dx=1.0, dy=1.0, dz=1.0, n_views=24,
                        nu=45, nv=37, du=1.6, dv=1.6, dso=120.0, dsd=240.0, M=4, N=4,
                        angles=0.05 + np.arange(24) * (2 * math.pi / 24)),
+    # Sec. 5, Table 1 case 1: 256^3 (1 mm), 360 views at 1 deg, 400^2 detector of
+    # 1 mm, source 1536 mm / detector 1000 mm from the centre; M = 5 groups of 72
+    # views (a seeded random partition, as in Sec. 5), N = 8
+    "paper_case1": dict(kind="cone3d", nx=256, ny=256, nz=256, dx=1.0, dy=1.0, dz=1.0,
+                        n_views=360, nu=400, nv=400, du=1.0, dv=1.0, dso=1536.0, dsd=2536.0,
+                        M=5, N=8),
     # config-2 workload: 256^3, 360 views, 256^2 detector at 1.6 mm, DSO 500 / DSD 1000
     "config2": dict(kind="cone3d", nx=256, ny=256, nz=256, dx=1.0, dy=1.0, dz=1.0,
                     n_views=360, nu=256, nv=256, du=1.6, dv=1.6, dso=500.0, dsd=1000.0, M=8, N=8),
 }
+
+
+def paper_partition(seed=5):
+    """360 views in 5 equal random groups (Sec. 5's random partition)."""
+    vb = np.repeat(np.arange(5, dtype=np.int32), 72)
+    np.random.default_rng(seed).shuffle(vb)
+    return vb
 
 
 def spec(name, **over):
