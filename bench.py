@@ -90,6 +90,8 @@ def parse():
                     help="run FP and BP as two kernels (to time them apart)")
     ap.add_argument("--paper-scale", default="case1,case2",
                     help="paper-scale cases to time (comma list of case1, case2; 'off')")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the BF16-storage, TV-prox and autograd legs")
     return ap.parse_args()
 
 
@@ -296,6 +298,10 @@ def run_cuda(args):
                "h2d_bytes_per_step": int(gg.n_rows * 4), "d2h_bytes_per_step": int(gg.n_cols * 4),
                "api": "bsgd_solve (1 epoch per call, pinned host y and x, fixed mu)"}
 
+    extra = None
+    if not args.no_extra and rank == 0 and world == 1:
+        extra = extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks)
+
     paper = None
     if args.paper_scale != "off" and rank == 0 and world == 1:
         paper = paper_scale_leg(B, torch, dev, [c for c in args.paper_scale.split(",") if c])
@@ -323,7 +329,7 @@ def run_cuda(args):
             "gpu_launches": int(launches), "stages_ms": stages,
             "kernels": "split FP / BP" if args.split else "fused FP+residual+BP",
             "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-            "serving": serving, "paper_scale": paper,
+            "serving": serving, "paper_scale": paper, "rows": extra,
         }
         print(json.dumps(line))
     if world > 1:
@@ -338,6 +344,92 @@ def serve_geometry(n, views):
     h = 256.0 / n
     return dict(kind="cone3d", nx=n, ny=n, nz=n, dx=h, dy=h, dz=h, n_views=views, nu=n, nv=n,
                 du=1.6 * h, dv=1.6 * h, dso=500.0, dsd=1000.0)
+
+
+# Autograd workload: a batch of 16 volumes of 128^3 (1 mm), 180 views over
+# 360 deg, 192^2 detector of 1.6 mm, DSO 500 / DSD 1000.
+AUTOGRAD_GEOM = dict(kind="cone3d", nx=128, ny=128, nz=128, dx=1.0, dy=1.0, dz=1.0, n_views=180,
+                     nu=192, nv=192, du=1.6, dv=1.6, dso=500.0, dsd=1000.0)
+AUTOGRAD_BATCH = 16
+
+
+def epoch_rate(B, torch, dev, gg, y, prm, warm=2, epochs=3):
+    """(GVox-ray/s, profile) of whole epochs of a fresh state."""
+    st = B.State(gg, prm, y)
+    x = torch.zeros(gg.n_cols, device=dev,
+                    dtype={B.F32: torch.float32, B.BF16: torch.bfloat16, B.F16: torch.float16}[prm.storage])
+    for _ in range(warm):
+        st.block_step(x, ITERS_PER_EPOCH)
+    torch.cuda.synchronize()
+    q0 = st.query()
+    st.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(epochs):
+        st.block_step(x, ITERS_PER_EPOCH)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = st.read_profile()
+    ms = e0.elapsed_time(e1)
+    upd = st.query()["updates"] - q0["updates"]
+    st.close()
+    return upd / (ms * 1e-3) / 1e9, prof, ms / epochs
+
+
+def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks):
+    """Measurements of the other rows of the hot path: the block update and the
+    TV prox against the HBM roofline, BF16 storage, the autograd projector."""
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {}
+    # a7: block update, 20 B per voxel of the slab (read x, g, gT; write x, xT)
+    vox_j = gg.n_cols // N
+    ms_u = prof["update"]["ms"] / max(prof["update"]["launches"], 1)
+    gbs = 20.0 * vox_j / (ms_u * 1e-3) / 1e9
+    out["a7_update"] = {"ms_per_launch": round(ms_u, 4), "bytes_per_launch": 20 * vox_j,
+                        "achieved_gbs": round(gbs, 1), "peak_gbs": hbm, "frac": round(gbs / hbm, 4),
+                        "bound": "hbm"}
+    ms_s = prof["sample"]["ms"] / max(prof["sample"]["launches"], 1)
+    out["a2_a3_sample"] = {"ms_per_launch": round(ms_s, 4), "bound": "latency (one CTA)"}
+    # P: the same workload with BF16 storage (FP32 arithmetic)
+    prm16 = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu,
+                          pair_sampling=B.PAIRS_RESIDUAL, storage=B.BF16, seed=1)
+    v16, _, ms16 = epoch_rate(B, torch, dev, gg, y, prm16)
+    out["P_bf16_storage"] = {"value": round(v16, 3), "unit": UNIT, "ms_per_epoch": round(ms16, 3)}
+    # a9: TV prox (FGP, 20 iterations) once per epoch; algorithmic bytes: 72 B
+    # per voxel and FGP iteration (primal: b, r_xyz read, u written; dual: u,
+    # r_xyz, p_xyz read, p_xyz, r_xyz written) + 80 B per voxel for the set-up
+    # and the final primal (the float4 layout of the dual fields moves ~100 B)
+    prmtv = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu,
+                          pair_sampling=B.PAIRS_RESIDUAL, tv_lambda=1e-3, tv_iters=20, seed=1)
+    _, ptv, _ = epoch_rate(B, torch, dev, gg, y, prmtv, warm=1, epochs=2)
+    ms_tv = ptv["tv"]["ms"] / max(1, ptv["tv"]["launches"] // 43)
+    btv = gg.n_cols * (72 * 20 + 80)
+    out["a9_tv_prox"] = {"ms_per_prox": round(ms_tv, 3), "bytes_per_prox": btv,
+                         "achieved_gbs": round(btv / (ms_tv * 1e-3) / 1e9, 1), "peak_gbs": hbm,
+                         "frac": round(btv / (ms_tv * 1e-3) / 1e9 / hbm, 4), "bound": "hbm",
+                         "fgp_iterations": 20}
+    # D: Projector forward + backward on a batch
+    from paper_1903_11874_gb300.autograd import Projector
+    ga = B.Geometry(M=1, N=1, **AUTOGRAD_GEOM)
+    per_vol = B.bsgd_count_updates(ga)
+    xb = torch.rand((AUTOGRAD_BATCH,) + tuple(ga.vol_shape), device=dev, requires_grad=True)
+    for _ in range(2):
+        Projector.apply(xb, ga).sum().backward()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        Projector.apply(xb, ga).sum().backward()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_ag = e0.elapsed_time(e1) / reps
+    out["D_autograd"] = {"batch": AUTOGRAD_BATCH, "volume": "128^3", "views": 180, "detector": "192^2",
+                         "ms_per_forward_backward": round(ms_ag, 3),
+                         "value": round(2 * per_vol * AUTOGRAD_BATCH / (ms_ag * 1e-3) / 1e9, 3),
+                         "unit": UNIT}
+    ga.close()
+    return out
 
 
 def paper_scale_leg(B, torch, dev, cases, warm=2, iters=10):

@@ -194,6 +194,17 @@ struct SolveDev {
     double *eud;       // Algorithm 3: effective update direction of the window (or null)
 };
 
+// Workspace of one TV prox (tv.cu): the input image b and the primal u (FP32),
+// the dual p and its extrapolation r (one float4 per voxel).
+struct TvWork {
+    float *b = nullptr, *u = nullptr;
+    float4 *p = nullptr, *r = nullptr;
+};
+bsgd_status tv_work_alloc(const bsgd_geometry *g, TvWork &w);
+void tv_work_free(TvWork &w);
+bsgd_status tv_prox_run(const bsgd_geometry *g, void *x, bsgd_dtype xt, double kappa, int iters,
+                        cudaStream_t st, void *xlo, const TvWork &w);
+
 // Sub-detector cell rectangle (Fig. 2): halves in u for 2 cells, quadrants
 // (v half * 2 + u half) for 4.
 __host__ __device__ inline void cell_rect(int nu, int nv, int n_cells, int c, Band &b) {

@@ -692,6 +692,7 @@ struct bsgd_state {
     int auto_win = 0;            // epochs per test (0: off)
     double *eud = nullptr, *eud_prev = nullptr, *am_part = nullptr;
     AutoMuHist *am = nullptr;
+    TvWork tv;                   // BSGD-TV prox workspace (tv_lambda > 0)
     SolveDev dev{};
     // tracing: event pairs per stage (a pool reused after each read)
     bool profiling = false;
@@ -739,6 +740,7 @@ static void free_state(bsgd_state *s) {
                     s->wband, s->d_iter, s->trace, s->replay, s->updates, s->eud,
                     s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) cudaFree(p);
+    tv_work_free(s->tv);
     delete s;
 }
 
@@ -877,6 +879,8 @@ static bsgd_status check_params(const bsgd_geometry *g, const bsgd_solve_params 
         return fail(BSGD_ERR_INVALID_ARG, "residual sampling supports M * N <= 2048");
     if (p->tv_lambda < 0 || (p->tv_lambda > 0 && p->tv_iters < 1))
         return fail(BSGD_ERR_INVALID_ARG, "tv_lambda >= 0 and tv_iters >= 1");
+    if (p->tv_lambda > 0 && g->desc.nz > 65535)
+        return fail(BSGD_ERR_INVALID_ARG, "the TV prox supports nz <= 65535");
     if (p->auto_mu) {
         if (!(p->auto_eps > 0) || !(p->auto_delta > 0 && p->auto_delta < 1) || !(p->auto_t1 > 0) ||
             p->auto_window < 0 || !std::isfinite(p->auto_t2))
@@ -888,10 +892,6 @@ static bsgd_status check_params(const bsgd_geometry *g, const bsgd_solve_params 
     return BSGD_OK;
 }
 
-namespace bsgd {
-bsgd_status tv_prox_impl(const bsgd_geometry *g, void *x, bsgd_dtype xt, double kappa, int iters,
-                         cudaStream_t st, void *xlo);
-}
 
 // Update counts per (J, view, cell) and, for Algorithm 2, the geometric cell
 // weights w(a, c, J) = 1^T A_(a,c)^J 1 (an FP of J's indicator summed per
@@ -1003,6 +1003,7 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         (s->st != BSGD_F32 && (e = dalloc(&s->xlo, C * es))) ||
         (g->desc.nz > 1 && (e = dalloc(&s->xT, C * es))) ||
         (g->desc.nz > 1 && (e = dalloc((void **)&s->gT, C * 4))) ||
+        (p->tv_lambda > 0 && (e = tv_work_alloc(g, s->tv))) ||
         (p->auto_mu && ((e = dalloc((void **)&s->eud, 8 * (size_t)C)) ||
                         (e = dalloc((void **)&s->eud_prev, 8 * (size_t)C)) ||
                         (e = dalloc((void **)&s->am_part, 8 * 3 * (size_t)kAutoParts)) ||
@@ -1252,7 +1253,7 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
     }
     if (s->p.tv_lambda > 0 && s->iters % s->epoch_len == 0) {
         b = stage_begin(s, st);
-        BSGD_TRY(tv_prox_impl(g, x, s->st, s->mu * s->p.tv_lambda, s->p.tv_iters, st, s->xlo));
+        BSGD_TRY(tv_prox_run(g, x, s->st, s->mu * s->p.tv_lambda, s->p.tv_iters, st, s->xlo, s->tv));
         BSGD_TRY(sync_xT(s, x, st));
         stage_end(s, BSGD_STAGE_TV, b, 2 * s->p.tv_iters + 3, st);
     }
