@@ -44,6 +44,11 @@ UNIT = "GVox-ray/s"
 # the next crossing, the segment difference, the accumulate / weight product and
 # the recomputed crossing.
 ALU_OPS_PER_UPDATE = 5
+# DRAM bytes (read + write) per launch of the fused kernel, mean over the 64
+# launches of one epoch of this workload, from one ncu capture of the current
+# kernel (profiles/fpbp_solve_kernel_cone256_dram_traffic.md); null for the
+# split kernels, which were not captured.
+TRAFFIC_PER_LAUNCH = {"fpbp": 66_768_228}
 
 
 # Serving workload: Poisson arrivals (20 / s), request sizes n^3 with (256 / n) mm
@@ -262,7 +267,7 @@ def run_cuda(args):
         "bound": "alu", "kernel": "%s_solve_kernel" % dom,
         "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
         "unit": "T FP32-pipe instr/s (%d per update)" % ALU_OPS_PER_UPDATE,
-        "frac": round(achieved / alu_peak, 4), "traffic": None,
+        "frac": round(achieved / alu_peak, 4), "traffic": TRAFFIC_PER_LAUNCH.get(dom),
         "peak_source": "152 SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % sm_max,
         "launch_ms": round(launch_ms, 4), "updates_per_launch": int(upd_per_launch),
         "hbm_algorithmic_gbs": round(hbm_ach, 1), "hbm_peak_gbs": hbm_peak,
