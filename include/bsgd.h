@@ -280,6 +280,11 @@ typedef struct {
  * Initial state is Algorithm 1's: g = 0, z = 0, r = y; x starts at 0 (the caller
  * passes x, zeroed, to bsgd_block_step). Computes mu by power iteration for the
  * STRIP / BLOCK rules. Synchronous.
+ * Memory: the state's arrays come from a stream-ordered pool per device, owned
+ * by the library, that keeps up to 32 GiB of freed memory for reuse by later
+ * states (so a state per call costs no page mapping once the pool is warm); the
+ * update counts and cell weights are computed once per geometry and kept with
+ * it (destroy a geometry only after its states).
  * Errors: INVALID_ARG (alpha, gamma outside (0, 1], residual pair sampling with
  * more than one pair per iteration, n_cells not 2 (2D) or 4 (3D) with cells),
  * OOM, CUDA.

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 
 #include "siddon_device.cuh"
 
@@ -733,13 +734,63 @@ static void stage_end(bsgd_state *s, int stage, cudaEvent_t b, int launches, cud
     s->launches[stage] += launches;
 }
 
+// Solver states and the one-call solver take their device memory from a
+// stream-ordered pool per device that keeps up to kPoolKeep bytes of freed
+// memory for reuse, so creating a state for every call costs no page mapping
+// once the pool is warm (cudaMalloc / cudaFree of ~2 GB took ~4 ms per call).
+constexpr uint64_t kPoolKeep = 32ull << 30;
+
+static bsgd_status state_pool(cudaMemPool_t *out) {
+    static std::mutex mu;
+    static std::map<int, cudaMemPool_t> pools;
+    int dev = 0;
+    BSGD_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = pools.find(dev);
+    if (it == pools.end()) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        BSGD_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = kPoolKeep;
+        BSGD_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        it = pools.emplace(dev, pool).first;
+    }
+    *out = it->second;
+    return BSGD_OK;
+}
+
+// Allocation from the pool, ordered on stream st.
+static bsgd_status palloc(void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    cudaMemPool_t pool = nullptr;
+    BSGD_TRY(state_pool(&pool));
+    cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), pool, st);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? BSGD_ERR_OOM : BSGD_ERR_CUDA,
+                    std::string("pool allocation of ") + std::to_string(bytes) +
+                        " bytes: " + cudaGetErrorString(e));
+    }
+    return BSGD_OK;
+}
+
+// Return pool memory; callers have synchronised the work that used it.
+static void pfree(void *p) {
+    if (p) cudaFreeAsync(p, 0);
+}
+
 static void free_state(bsgd_state *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
-    // counts and cw belong to the geometry's cache
+    // counts and cw belong to the geometry's cache; replay is a plain allocation
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->trace, s->replay, s->updates, s->eud,
+                    s->wband, s->d_iter, s->trace, s->updates, s->eud,
                     s->eud_prev, s->am_part, s->am};
-    for (void *p : ptrs) cudaFree(p);
+    for (void *p : ptrs) pfree(p);
+    cudaFree(s->replay);
     tv_work_free(s->tv);
     delete s;
 }
@@ -991,23 +1042,24 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     const size_t es = dtype_size(s->st);
     const int N = g->N, M = g->M, V = g->desc.n_views;
     bsgd_status e = BSGD_OK;
-    if ((e = dalloc(&s->y, R * es)) || (e = dalloc(&s->z, (size_t)N * R * es)) ||
-        (e = dalloc(&s->rt, (size_t)N * R * es)) || (e = dalloc(&s->r, R * es)) ||
-        (e = dalloc((void **)&s->grad, C * 4)) || (e = dalloc((void **)&s->S, 8 * (size_t)M * g->desc.nv)) ||
-        (e = dalloc((void **)&s->d_mu, 8)) || (e = dalloc((void **)&s->work, sizeof(Work))) ||
-        (e = dalloc((void **)&s->cells, 4 * (size_t)kMaxPairs * g->max_views)) ||
-        (e = dalloc((void **)&s->wband, 4 * g->wband.size())) ||
-        (e = dalloc((void **)&s->d_iter, 8)) ||
-        (e = dalloc((void **)&s->trace, 4 * (size_t)s->trace_cap * s->stride)) ||
-        (e = dalloc((void **)&s->updates, 8)) ||
-        (s->st != BSGD_F32 && (e = dalloc(&s->xlo, C * es))) ||
-        (g->desc.nz > 1 && (e = dalloc(&s->xT, C * es))) ||
-        (g->desc.nz > 1 && (e = dalloc((void **)&s->gT, C * 4))) ||
+    if ((e = palloc(&s->y, R * es, st)) || (e = palloc(&s->z, (size_t)N * R * es, st)) ||
+        (e = palloc(&s->rt, (size_t)N * R * es, st)) || (e = palloc(&s->r, R * es, st)) ||
+        (e = palloc((void **)&s->grad, C * 4, st)) || (e = palloc((void **)&s->S, 8 * (size_t)M * g->desc.nv, st)) ||
+        (e = palloc((void **)&s->d_mu, 8, st)) || (e = palloc((void **)&s->work, sizeof(Work), st)) ||
+        (e = palloc((void **)&s->cells, 4 * (size_t)kMaxPairs * g->max_views, st)) ||
+        (e = palloc((void **)&s->wband, 4 * g->wband.size(), st)) ||
+        (e = palloc((void **)&s->d_iter, 8, st)) ||
+        (e = palloc((void **)&s->trace, 4 * (size_t)s->trace_cap * s->stride, st)) ||
+        (e = palloc((void **)&s->updates, 8, st)) ||
+        (s->st != BSGD_F32 && (e = palloc(&s->xlo, C * es, st))) ||
+        (g->desc.nz > 1 && (e = palloc(&s->xT, C * es, st))) ||
+        (g->desc.nz > 1 && (e = palloc((void **)&s->gT, C * 4, st))) ||
         (p->tv_lambda > 0 && (e = tv_work_alloc(g, s->tv))) ||
-        (p->auto_mu && ((e = dalloc((void **)&s->eud, 8 * (size_t)C)) ||
-                        (e = dalloc((void **)&s->eud_prev, 8 * (size_t)C)) ||
-                        (e = dalloc((void **)&s->am_part, 8 * 3 * (size_t)kAutoParts)) ||
-                        (e = dalloc((void **)&s->am, sizeof(AutoMuHist)))))) {
+        (p->auto_mu && ((e = palloc((void **)&s->eud, 8 * (size_t)C, st)) ||
+                        (e = palloc((void **)&s->eud_prev, 8 * (size_t)C, st)) ||
+                        (e = palloc((void **)&s->am_part, 8 * 3 * (size_t)kAutoParts, st)) ||
+                        (e = palloc((void **)&s->am, sizeof(AutoMuHist), st))))) {
+        cudaStreamSynchronize(st);
         free_state(s);
         return e;
     }
@@ -1389,18 +1441,18 @@ extern "C" bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_param
     auto body = [&]() -> bsgd_status {
         const void *yy = y;
         if (yh) {
-            BSGD_TRY(dalloc(&dy, R * dtype_size(yt)));
+            BSGD_TRY(palloc(&dy, R * dtype_size(yt), st));
             BSGD_CUDA(cudaMemcpyAsync(dy, y, R * dtype_size(yt), cudaMemcpyHostToDevice, st));
             yy = dy;
         }
         BSGD_TRY(bsgd_state_create(g, p, yy, yt, stream, &s));
         const bsgd_dtype sd = (bsgd_dtype)p->storage;
-        BSGD_TRY(dalloc(&xs, C * dtype_size(sd)));
+        BSGD_TRY(palloc(&xs, C * dtype_size(sd), st));
         BSGD_CUDA(cudaMemsetAsync(xs, 0, C * dtype_size(sd), st));
         BSGD_TRY(bsgd_block_step(s, xs, p->epochs * s->epoch_len, stream));
         void *xo = x;
         if (xh) {
-            BSGD_TRY(dalloc(&dx, C * dtype_size(xt)));
+            BSGD_TRY(palloc(&dx, C * dtype_size(xt), st));
             xo = dx;
         }
         BSGD_TRY(convert(xs, sd, xo, xt, C, st));
@@ -1412,8 +1464,8 @@ extern "C" bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_param
     e = body();
     cudaStreamSynchronize(st);
     if (s) bsgd_state_destroy(s);
-    cudaFree(dy);
-    cudaFree(dx);
-    cudaFree(xs);
+    pfree(dy);
+    pfree(dx);
+    pfree(xs);
     return e;
 }
