@@ -194,6 +194,12 @@ struct SolveDev {
     double *eud;       // Algorithm 3: effective update direction of the window (or null)
 };
 
+// Device memory from the library's stream-ordered pool (solver.cu), and the
+// stream-ordered release of a solver state (serving).
+bsgd_status pool_alloc(void **p, size_t bytes, cudaStream_t st);
+void pool_free(void *p, cudaStream_t st);
+void state_release(bsgd_state *s, cudaStream_t st);
+
 // Workspace of one TV prox (tv.cu): the input image b and the primal u (FP32),
 // the dual p and its extrapolation r (one float4 per voxel).
 struct TvWork {

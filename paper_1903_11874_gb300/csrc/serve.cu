@@ -54,12 +54,14 @@ struct Request {
     int64_t target = 0, done = 0; // iterations
     ReqStatus status = kQueued;
     std::string error;
+    std::string geo_key;          // geometry cache entry this request holds
     bsgd_geometry *g = nullptr;
     bsgd_state *st = nullptr;
-    void *x = nullptr;            // device image (storage type)
-    float *xf = nullptr;          // device float copy for the result
-    float *stage = nullptr;       // pinned host staging of the result
-    unsigned long long *upd_host = nullptr;  // pinned
+    void *x = nullptr;            // device image (storage type), from the pool
+    float *xf = nullptr;          // device float copy for the result, from the pool
+    float *stage = nullptr;       // pinned host staging of the result (+ update count)
+    size_t stage_bytes = 0;
+    unsigned long long *upd_host = nullptr;  // inside stage
     cudaEvent_t ev = nullptr;
     double t_submit = 0, t_done = 0;
     bsgd_report rep{};
@@ -81,6 +83,16 @@ struct bsgd_server {
     std::vector<std::thread> admit_thr;
     std::thread round_thr;
     std::map<std::string, double> mu_cache;  // step size per geometry and step rule
+    // geometries shared by requests of the same set-up (their update counts are
+    // computed once): entry -> (geometry, requests holding it, last use)
+    struct GeoEntry {
+        bsgd_geometry *g = nullptr;
+        int refs = 0;
+        int64_t last = 0;
+    };
+    std::map<std::string, GeoEntry> geo_cache;
+    int64_t geo_clock = 0;
+    std::multimap<size_t, float *> pinned_free;   // reusable pinned staging buffers
     cudaStream_t round_stream = nullptr;
     std::vector<cudaStream_t> admit_streams;
     ReqDesc *d_table = nullptr;
@@ -100,16 +112,111 @@ struct bsgd_server {
 
 namespace {
 
-void free_request_gpu(Request *r) {
-    if (r->st) bsgd_state_destroy(r->st);
-    if (r->g) bsgd_geometry_destroy(r->g);
-    cudaFree(r->x);
-    cudaFree(r->xf);
-    if (r->stage) cudaFreeHost(r->stage);
-    if (r->upd_host) cudaFreeHost(r->upd_host);
+constexpr size_t kGeoKeep = 16;   // unreferenced geometries kept for reuse
+
+// Key of a geometry: everything its tables depend on.
+std::string geometry_key(const Request *r) {
+    const bsgd_geometry_desc &d = r->desc;
+    std::string k;
+    auto put = [&](const void *p, size_t n) { k.append((const char *)p, n); };
+    put(&d.kind, sizeof d.kind);
+    put(&d.nx, 3 * sizeof(int));
+    put(&d.dx, 3 * sizeof(double));
+    put(&d.n_views, sizeof(int));
+    put(&d.nu, 2 * sizeof(int));
+    put(&d.du, 4 * sizeof(double));
+    if (d.angles) put(d.angles, sizeof(double) * d.n_views);
+    if (d.view_block) put(d.view_block, sizeof(int32_t) * d.n_views);
+    put(&r->M, sizeof(int));
+    put(&r->N, sizeof(int));
+    return k;
+}
+
+// The geometry of r's set-up, shared through the server's cache.
+bsgd_status acquire_geometry(bsgd_server *S, Request *r) {
+    r->geo_key = geometry_key(r);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->geo_cache.find(r->geo_key);
+        if (it != S->geo_cache.end()) {
+            it->second.refs++;
+            it->second.last = ++S->geo_clock;
+            r->g = it->second.g;
+            return BSGD_OK;
+        }
+    }
+    bsgd_geometry *g = nullptr;
+    BSGD_TRY(bsgd_geometry_create(&r->desc, r->M, r->N, &g));
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto &e = S->geo_cache[r->geo_key];
+    if (e.g) {                       // another admission thread built it meanwhile
+        bsgd_geometry_destroy(g);
+    } else {
+        e.g = g;
+    }
+    e.refs++;
+    e.last = ++S->geo_clock;
+    r->g = e.g;
+    return BSGD_OK;
+}
+
+// Drop r's hold on its geometry; beyond kGeoKeep unreferenced entries the
+// least recently used one is destroyed. Called without S->mu held.
+void release_geometry(bsgd_server *S, Request *r) {
+    if (!r->g) return;
+    bsgd_geometry *drop = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->geo_cache.find(r->geo_key);
+        if (it != S->geo_cache.end()) it->second.refs--;
+        size_t idle = 0;
+        auto oldest = S->geo_cache.end();
+        for (auto jt = S->geo_cache.begin(); jt != S->geo_cache.end(); ++jt) {
+            if (jt->second.refs > 0) continue;
+            ++idle;
+            if (oldest == S->geo_cache.end() || jt->second.last < oldest->second.last) oldest = jt;
+        }
+        if (idle > kGeoKeep) {
+            drop = oldest->second.g;
+            S->geo_cache.erase(oldest);
+        }
+    }
+    if (drop) bsgd_geometry_destroy(drop);
+    r->g = nullptr;
+}
+
+float *take_pinned(bsgd_server *S, size_t bytes) {
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->pinned_free.lower_bound(bytes);
+        if (it != S->pinned_free.end() && it->first <= 2 * bytes) {
+            float *p = it->second;
+            S->pinned_free.erase(it);
+            return p;
+        }
+    }
+    float *p = nullptr;
+    if (cudaHostAlloc((void **)&p, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+// Release what a request holds. Its device work is ordered on `st` (the round
+// stream once it has been resident), so the pool memory is freed in stream
+// order there; nothing here synchronises the device.
+void free_request_gpu(bsgd_server *S, Request *r, cudaStream_t st) {
+    if (r->st) state_release(r->st, st);
+    pool_free(r->x, st);
+    pool_free(r->xf, st);
+    release_geometry(S, r);
+    if (r->stage) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->pinned_free.emplace(r->stage_bytes, r->stage);
+    }
     if (r->ev) cudaEventDestroy(r->ev);
     r->st = nullptr;
-    r->g = nullptr;
     r->x = r->xf = nullptr;
     r->stage = nullptr;
     r->upd_host = nullptr;
@@ -151,16 +258,16 @@ bsgd_status admit_one(bsgd_server *S, Request *r, cudaStream_t stream) {
             prm.mu = it->second;
         }
     }
-    BSGD_TRY(bsgd_geometry_create(&r->desc, r->M, r->N, &r->g));
+    BSGD_TRY(acquire_geometry(S, r));
     const int64_t R = r->g->n_rows(), C = r->g->n_cols();
     const size_t ys = dtype_size(r->yt), es = dtype_size((bsgd_dtype)r->p.storage);
     void *dy = nullptr;
-    BSGD_CUDA(cudaMalloc(&dy, R * ys));
+    BSGD_TRY(pool_alloc(&dy, R * ys, stream));
     cudaError_t e = cudaMemcpyAsync(dy, r->y.data(), R * ys, cudaMemcpyHostToDevice, stream);
     bsgd_status st = e == cudaSuccess ? BSGD_OK : cuda_fail(e, "copy of y");
     if (!st) st = bsgd_state_create(r->g, &prm, dy, r->yt, stream, &r->st);
     cudaStreamSynchronize(stream);
-    cudaFree(dy);
+    pool_free(dy, stream);
     BSGD_TRY(st);
     if (!key.empty()) {
         bsgd_report rep{};
@@ -171,11 +278,13 @@ bsgd_status admit_one(bsgd_server *S, Request *r, cudaStream_t stream) {
     }
     r->y.clear();
     r->y.shrink_to_fit();
-    BSGD_CUDA(cudaMalloc(&r->x, C * es));
-    BSGD_CUDA(cudaMalloc((void **)&r->xf, C * 4));
+    BSGD_TRY(pool_alloc(&r->x, C * es, stream));
+    BSGD_TRY(pool_alloc((void **)&r->xf, C * 4, stream));
     BSGD_CUDA(cudaMemsetAsync(r->x, 0, C * es, stream));
-    BSGD_CUDA(cudaHostAlloc((void **)&r->stage, C * 4, cudaHostAllocDefault));
-    BSGD_CUDA(cudaHostAlloc((void **)&r->upd_host, 8, cudaHostAllocDefault));
+    r->stage_bytes = (size_t)C * 4 + 64;
+    r->stage = take_pinned(S, r->stage_bytes);
+    if (!r->stage) return fail(BSGD_ERR_OOM, "pinned staging buffer");
+    r->upd_host = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(r->stage) + (size_t)C * 4 + 32);
     BSGD_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
     BSGD_CUDA(cudaStreamSynchronize(stream));
     ReqDesc tmp;
@@ -220,7 +329,7 @@ void admission_loop(bsgd_server *S, cudaStream_t stream) {
                 S->admitted++;
             }
         }
-        if (st) free_request_gpu(r);
+        if (st) free_request_gpu(S, r, stream);
         S->cv.notify_all();
     }
 }
@@ -352,7 +461,7 @@ void round_loop(bsgd_server *S) {
             const int64_t C = r->g->n_cols();
             std::memcpy(r->x_out, r->stage, C * 4);
             const unsigned long long upd = *r->upd_host;
-            free_request_gpu(r);
+            free_request_gpu(S, r, S->round_stream);
             std::lock_guard<std::mutex> lk(S->mu);
             r->t_done = now_s();
             r->rep.iteration = r->target;
@@ -453,9 +562,12 @@ extern "C" bsgd_status bsgd_server_destroy(bsgd_server *S) {
     cudaSetDevice(S->prm.device);
     cudaStreamSynchronize(S->round_stream);
     for (auto &kv : S->all) {
-        free_request_gpu(kv.second);
+        free_request_gpu(S, kv.second, S->round_stream);
         delete kv.second;
     }
+    cudaStreamSynchronize(S->round_stream);
+    for (auto &kv : S->geo_cache) bsgd_geometry_destroy(kv.second.g);
+    for (auto &kv : S->pinned_free) cudaFreeHost(kv.second);
     if (S->graph) cudaGraphExecDestroy(S->graph);
     cudaFree(S->d_table);
     cudaFree(S->d_ctl);

@@ -783,6 +783,13 @@ static void pfree(void *p) {
     if (p) cudaFreeAsync(p, 0);
 }
 
+namespace bsgd {
+bsgd_status pool_alloc(void **p, size_t bytes, cudaStream_t st) { return palloc(p, bytes, st); }
+void pool_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+}  // namespace bsgd
+
 static void free_state(bsgd_state *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     // counts and cw belong to the geometry's cache; replay is a plain allocation
@@ -1138,6 +1145,26 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     *out = s;
     return BSGD_OK;
 }
+
+namespace bsgd {
+// Release a state whose work on stream st is the last that used it (serving):
+// its pool memory is freed in stream order on st, without a device-wide
+// synchronisation. States with TV workspace or a replay buffer synchronise st.
+void state_release(bsgd_state *s, cudaStream_t st) {
+    if (!s) return;
+    if (s->tv.b || s->replay) {
+        cudaStreamSynchronize(st);
+        free_state(s);
+        return;
+    }
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
+    void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
+                    s->wband, s->d_iter, s->trace, s->updates, s->eud,
+                    s->eud_prev, s->am_part, s->am};
+    for (void *p : ptrs) pool_free(p, st);
+    delete s;
+}
+}  // namespace bsgd
 
 extern "C" bsgd_status bsgd_state_destroy(bsgd_state *s) {
     if (!s) return fail(BSGD_ERR_INVALID_ARG, "state is NULL");
