@@ -93,6 +93,9 @@ typedef struct {
     int block_axis;             /* 1 (y strips, 2D) or 2 (z slabs, 3D)             */
     int max_views_per_block;
     int64_t max_block_cols;     /* voxels in the largest column block              */
+    int64_t compact_rows;       /* rows of the compact per-block sinograms z^j and
+                                   r~^j of a solver state: sum over (view, block)
+                                   of the block's detector band (<= N * n_rows)    */
 } bsgd_geometry_info;
 
 const char *bsgd_last_error(void);
@@ -275,7 +278,9 @@ typedef struct {
 /*
  * Create solver state for y (device, n_rows elements of type yt, copied into
  * the state's storage type). The state holds z^j and the residual snapshots
- * (N * n_rows each), r, the aggregated gradient g (FP32), FP64 residual-norm
+ * r~^j for the rows of each block's detector band only (compact_rows each in
+ * all; a row outside block j's band has z^j = 0), r, the aggregated gradient g
+ * (FP32), FP64 residual-norm
  * tables and the sampler's work list, all in library-owned device memory.
  * Initial state is Algorithm 1's: g = 0, z = 0, r = y; x starts at 0 (the caller
  * passes x, zeroed, to bsgd_block_step). Computes mu by power iteration for the

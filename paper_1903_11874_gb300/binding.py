@@ -63,6 +63,7 @@ class GeometryInfo(ctypes.Structure):
         ("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64),
         ("M", ctypes.c_int), ("N", ctypes.c_int), ("block_axis", ctypes.c_int),
         ("max_views_per_block", ctypes.c_int), ("max_block_cols", ctypes.c_int64),
+        ("compact_rows", ctypes.c_int64),
     ]
 
 
@@ -262,6 +263,10 @@ class Geometry:
     @property
     def n_rows(self):
         return int(self.info.n_rows)
+
+    @property
+    def compact_rows(self):
+        return int(self.info.compact_rows)
 
     @property
     def n_cols(self):

@@ -64,6 +64,11 @@ struct DeviceGeom {
     const int *plane_start;    // N + 1 planes along the block axis
     const int *view_block;     // n_views
     const unsigned char *view_yfast;  // n_views: 1 if the view's rays run mostly along x
+    // Compact band storage of the per-block sinograms z^j and r~^j: the rows of
+    // view a inside block j's band (bands[a][j]) are stored from zoff[j][a] on,
+    // v-major within the band; rows outside the band hold 0 and are not stored.
+    const int64_t *zoff;       // N x n_views
+    int64_t zlen;              // elements of one compact array (all blocks)
     int nx, ny, nz;
     float hx, hy, hz;
     int nu, nv, n_views;
@@ -87,6 +92,8 @@ struct bsgd_geometry {
     std::vector<bsgd::ViewRay> rays;
     std::vector<bsgd::Band> bands;              // n_views x (N + 1), traversal bands
     std::vector<int> wband;                     // M x N x 2: exact v-band of the pair
+    std::vector<int64_t> zoff;                  // N x n_views: compact band offsets
+    int64_t zlen = 0;
     int device = 0;
     // device copies
     bsgd::ViewRay *d_rays = nullptr;
@@ -96,6 +103,7 @@ struct bsgd_geometry {
     int *d_plane_start = nullptr;
     int *d_view_block = nullptr;
     unsigned char *d_view_yfast = nullptr;
+    int64_t *d_zoff = nullptr;
     bsgd::DeviceGeom dg{};
     // Filled on first use by a solver state and kept for the geometry's life
     // (index: number of detector cells 1, 2 or 4): exact voxel-ray update
@@ -193,6 +201,10 @@ struct SolveDev {
     float *gT;         // their part of the aggregated gradient, [z][x][y]
     double *eud;       // Algorithm 3: effective update direction of the window (or null)
 };
+
+// Host tables of a geometry (rays, blocks, bands, compact band offsets) without
+// touching the GPU; bsgd_geometry_create adds the device copies (geometry.cu).
+bsgd_status build_host_tables(const bsgd_geometry_desc *desc, int M, int N, bsgd_geometry *g);
 
 // Device memory from the library's stream-ordered pool (solver.cu), and the
 // stream-ordered release of a solver state (serving).

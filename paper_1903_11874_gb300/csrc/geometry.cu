@@ -210,6 +210,7 @@ static void free_geometry(bsgd_geometry *g) {
     cudaFree(g->d_plane_start);
     cudaFree(g->d_view_block);
     cudaFree(g->d_view_yfast);
+    cudaFree(g->d_zoff);
     for (int k = 0; k < 5; ++k) {
         cudaFree(g->d_counts[k]);
         cudaFree(g->d_cw[k]);
@@ -217,13 +218,9 @@ static void free_geometry(bsgd_geometry *g) {
     delete g;
 }
 
-extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int M, int N,
-                                            bsgd_geometry **out) {
-    if (!out) return fail(BSGD_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
+namespace bsgd {
+bsgd_status build_host_tables(const bsgd_geometry_desc *desc, int M, int N, bsgd_geometry *g) {
     BSGD_TRY(validate(desc, M, N));
-    bsgd_geometry *g = new (std::nothrow) bsgd_geometry();
-    if (!g) return fail(BSGD_ERR_OOM, "host allocation failed");
     const bsgd_geometry_desc &d = *desc;
     g->desc = d;
     g->M = M;
@@ -329,6 +326,36 @@ extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int 
         }
     }
 
+    // ---- compact band storage: block j's rows of view a, band by band
+    g->zoff.assign((size_t)N * d.n_views, 0);
+    int64_t off = 0;
+    for (int j = 0; j < N; ++j) {
+        for (int a = 0; a < d.n_views; ++a) {
+            g->zoff[(size_t)j * d.n_views + a] = off;
+            const Band &b = g->bands[(size_t)a * stride + j];
+            if (b.u0 <= b.u1 && b.v0 <= b.v1) off += (int64_t)(b.u1 - b.u0 + 1) * (b.v1 - b.v0 + 1);
+        }
+    }
+    g->zlen = off;
+    return BSGD_OK;
+}
+}  // namespace bsgd
+
+extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int M, int N,
+                                            bsgd_geometry **out) {
+    if (!out) return fail(BSGD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    bsgd_geometry *g = new (std::nothrow) bsgd_geometry();
+    if (!g) return fail(BSGD_ERR_OOM, "host allocation failed");
+    {
+        bsgd_status st = build_host_tables(desc, M, N, g);
+        if (st) {
+            delete g;
+            return st;
+        }
+    }
+    const bsgd_geometry_desc &d = *desc;
+
     // ---- upload
     std::vector<int> bv((size_t)M * g->max_views, -1), bn(M);
     for (int i = 0; i < M; ++i) {
@@ -351,7 +378,8 @@ extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int 
         (st = upload((void **)&g->d_plane_start, g->plane_start.data(), (N + 1) * sizeof(int))) ||
         (st = upload((void **)&g->d_view_block, g->view_block.data(),
                      g->view_block.size() * sizeof(int))) ||
-        (st = upload((void **)&g->d_view_yfast, yfast.data(), yfast.size()))) {
+        (st = upload((void **)&g->d_view_yfast, yfast.data(), yfast.size())) ||
+        (st = upload((void **)&g->d_zoff, g->zoff.data(), g->zoff.size() * sizeof(int64_t)))) {
         free_geometry(g);
         return st;
     }
@@ -363,6 +391,8 @@ extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int 
     dg.plane_start = g->d_plane_start;
     dg.view_block = g->d_view_block;
     dg.view_yfast = g->d_view_yfast;
+    dg.zoff = g->d_zoff;
+    dg.zlen = g->zlen;
     dg.nx = d.nx;
     dg.ny = d.ny;
     dg.nz = d.nz;
@@ -400,6 +430,7 @@ extern "C" bsgd_status bsgd_geometry_get_info(const bsgd_geometry *g, bsgd_geome
     int64_t m = 0;
     for (int j = 0; j < g->N; ++j) m = std::max(m, g->block_cols(j));
     out->max_block_cols = m;
+    out->compact_rows = g->zlen;
     return BSGD_OK;
 }
 

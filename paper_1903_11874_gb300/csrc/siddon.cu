@@ -148,16 +148,24 @@ __device__ __forceinline__ void fp_solve_body(const DeviceGeom &G, const SolveDe
     }
     const int64_t row = act ? ((int64_t)a * G.nv + v) * G.nu + u : 0;
     T *z = reinterpret_cast<T *>(S.z);
+    bool in;
     if (!FUSED) {
-        if (act) stf(z + (int64_t)j * G.n_rows + row, zn);
+        if (act) stf(z + zslot(G, j, a, u, v, in), zn);
         return;
     }
     double dn = 0.0;
     if (act) {
-        stf(z + (int64_t)j * G.n_rows + row, zn);
+        stf(z + zslot(G, j, a, u, v, in), zn);
         zn = rnd(zn, z);
         float zs = 0.f;
-        for (int jj = 0; jj < G.N; ++jj) zs += jj == j ? zn : ldv(z + (int64_t)jj * G.n_rows + row);
+        for (int jj = 0; jj < G.N; ++jj) {   // z^jj is 0 outside block jj's band
+            if (jj == j) {
+                zs += zn;
+                continue;
+            }
+            const int64_t k = zslot(G, jj, a, u, v, in);
+            if (in) zs += ldv(z + k);
+        }
         T *r = reinterpret_cast<T *>(S.r);
         const float rn = rnd(ldf(reinterpret_cast<const T *>(S.y) + row) - zs, r);
         const float ro = ldv(r + row);
@@ -179,9 +187,11 @@ __device__ __forceinline__ void bp_solve_body(const DeviceGeom &G, const SolveDe
     if (!solve_pixel(G, S, tile, slot, p, a, i, j, u, v, act) || !act) return;
     const int64_t row = ((int64_t)a * G.nv + v) * G.nu + u;
     const T *r = reinterpret_cast<const T *>(S.r);
-    T *rt = reinterpret_cast<T *>(S.rt) + (int64_t)j * G.n_rows;
-    const float rv = ldv(r + row), ro = ldv(rt + row);
-    stf(rt + row, rv);
+    T *rt = reinterpret_cast<T *>(S.rt);
+    bool in;
+    const int64_t kt = zslot(G, j, a, u, v, in);
+    const float rv = ldv(r + row), ro = ldv(rt + kt);
+    stf(rt + kt, rv);
     const float dw = rv - ro;
     if (dw == 0.f) return;
     const bool yf = S.gT != nullptr && G.view_yfast[a];
@@ -220,18 +230,27 @@ __device__ __forceinline__ void fpbp_solve_body(const DeviceGeom &G, const Solve
     double dn = 0.0;
     float dw = 0.f;
     if (act) {
-        stf(z + (int64_t)j * G.n_rows + row, zn);
+        bool in;
+        const int64_t kj = zslot(G, j, a, u, v, in);
+        stf(z + kj, zn);
         zn = rnd(zn, z);
         float zs = 0.f;
-        for (int jj = 0; jj < G.N; ++jj) zs += jj == j ? zn : ldv(z + (int64_t)jj * G.n_rows + row);
+        for (int jj = 0; jj < G.N; ++jj) {   // z^jj is 0 outside block jj's band
+            if (jj == j) {
+                zs += zn;
+                continue;
+            }
+            const int64_t k = zslot(G, jj, a, u, v, in);
+            if (in) zs += ldv(z + k);
+        }
         T *r = reinterpret_cast<T *>(S.r);
-        T *rt = reinterpret_cast<T *>(S.rt) + (int64_t)j * G.n_rows;
+        T *rt = reinterpret_cast<T *>(S.rt);
         const float rn = rnd(ldf(reinterpret_cast<const T *>(S.y) + row) - zs, r);
         const float ro = ldv(r + row);
         stf(r + row, rn);
         dn = (double)rn * rn - (double)ro * ro;
-        dw = rn - ldv(rt + row);
-        stf(rt + row, rn);
+        dw = rn - ldv(rt + kj);
+        stf(rt + kj, rn);
     }
     for (int o = 16; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
     if ((threadIdx.x & 31) == 0 && act && dn != 0.0) atomicAdd(S.S + (size_t)i * G.nv + v, dn);

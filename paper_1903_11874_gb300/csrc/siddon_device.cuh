@@ -43,6 +43,14 @@ __device__ __forceinline__ float rnd(float v, const __half *) {
 
 constexpr float kInf = __builtin_huge_valf();
 
+// Index of row (a, u, v) in block j's compact sinogram (z^j, r~^j); `in`
+// tells whether the row lies in the block's band (outside it the value is 0).
+__device__ __forceinline__ int64_t zslot(const DeviceGeom &G, int j, int a, int u, int v, bool &in) {
+    const Band b = G.bands[(size_t)a * (G.N + 1) + j];
+    in = u >= b.u0 && u <= b.u1 && v >= b.v0 && v <= b.v1;
+    return G.zoff[(size_t)j * G.n_views + a] + (int64_t)(v - b.v0) * (b.u1 - b.u0 + 1) + (u - b.u0);
+}
+
 struct RayWalk {
     float tx, ty, tz;   // parameter left to the next interior plane per axis (INF: none)
     float te;           // parameter left to the exit face (INF until the exit axis has

@@ -295,7 +295,11 @@ __global__ void __launch_bounds__(256) residual_kernel(const DeviceGeom G, const
         for (int u = b.u0 + threadIdx.x; u <= b.u1; u += blockDim.x) {
             const int64_t row = base + u;
             float zs = 0.f;
-            for (int jj = 0; jj < G.N; ++jj) zs += ldv(z + (int64_t)jj * G.n_rows + row);
+            for (int jj = 0; jj < G.N; ++jj) {   // z^jj is 0 outside block jj's band
+                bool in;
+                const int64_t kz = zslot(G, jj, a, u, v, in);
+                if (in) zs += ldv(z + kz);
+            }
             const float rn = rnd(ldf(y + row) - zs, r);
             const float ro = ldv(r + row);
             if (rn != ro) {
@@ -1049,8 +1053,9 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     const size_t es = dtype_size(s->st);
     const int N = g->N, M = g->M, V = g->desc.n_views;
     bsgd_status e = BSGD_OK;
-    if ((e = palloc(&s->y, R * es, st)) || (e = palloc(&s->z, (size_t)N * R * es, st)) ||
-        (e = palloc(&s->rt, (size_t)N * R * es, st)) || (e = palloc(&s->r, R * es, st)) ||
+    const int64_t Z = g->zlen;   // compact band storage of z^j and r~^j
+    if ((e = palloc(&s->y, R * es, st)) || (e = palloc(&s->z, (size_t)Z * es, st)) ||
+        (e = palloc(&s->rt, (size_t)Z * es, st)) || (e = palloc(&s->r, R * es, st)) ||
         (e = palloc((void **)&s->grad, C * 4, st)) || (e = palloc((void **)&s->S, 8 * (size_t)M * g->desc.nv, st)) ||
         (e = palloc((void **)&s->d_mu, 8, st)) || (e = palloc((void **)&s->work, sizeof(Work), st)) ||
         (e = palloc((void **)&s->cells, 4 * (size_t)kMaxPairs * g->max_views, st)) ||
@@ -1073,8 +1078,8 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     auto init = [&]() -> bsgd_status {
         BSGD_TRY(convert(y, yt, s->y, s->st, R, st));
         BSGD_CUDA(cudaMemcpyAsync(s->r, s->y, R * es, cudaMemcpyDeviceToDevice, st));
-        BSGD_CUDA(cudaMemsetAsync(s->z, 0, (size_t)N * R * es, st));
-        BSGD_CUDA(cudaMemsetAsync(s->rt, 0, (size_t)N * R * es, st));
+        BSGD_CUDA(cudaMemsetAsync(s->z, 0, (size_t)Z * es, st));
+        BSGD_CUDA(cudaMemsetAsync(s->rt, 0, (size_t)Z * es, st));
         BSGD_CUDA(cudaMemsetAsync(s->grad, 0, C * 4, st));
         if (s->xlo) BSGD_CUDA(cudaMemsetAsync(s->xlo, 0, C * es, st));
         if (s->xT) BSGD_CUDA(cudaMemsetAsync(s->xT, 0, C * es, st));
@@ -1239,8 +1244,14 @@ size_t state_bytes(const bsgd_geometry_desc &d, int M, int N, const bsgd_solve_p
     }
     const size_t cells = p.cells == BSGD_CELLS_NONE ? 1 : (size_t)std::max(1, p.n_cells);
     const size_t stride = 1 + 2 * (size_t)P + (size_t)P * maxV;
+    // z^j and r~^j hold the rows of each block's band only (host tables)
+    size_t Z = (size_t)N * R;
+    {
+        bsgd_geometry tmp;
+        if (build_host_tables(&d, M, N, &tmp) == BSGD_OK) Z = (size_t)tmp.zlen;
+    }
     size_t b = 0;
-    b += R * es * (2 + 2 * (size_t)N);                 // y, r, z^j, r~^j
+    b += R * es * 2 + Z * es * 2;                      // y, r, z^j, r~^j
     b += C * 4;                                        // g
     if (es != 4) b += C * es;                          // low-order image term
     if (d.nz > 1) b += C * (es + 4);                   // y-fastest copies of x and g

@@ -251,3 +251,15 @@ def test_config2_first_iteration():
     assert rel_l2(got[vox], ref) <= 1e-5
     other = np.setdiff1d(np.arange(og.n_cols), vox)
     assert not got[other].any()
+
+
+@pytest.mark.parametrize("name,frac", [("cone_small", 1.0), ("config2", 0.35)])
+def test_compact_band_storage(name, frac):
+    """z^j and r~^j keep the rows of block j's band only: their length is the
+    sum over (view, block) of the band areas, i.e. the rays of all pairs, and
+    (for thin slabs) a small part of N full sinograms."""
+    s = spec(name)
+    gg = gpu_geom(s)
+    M, N = s["M"], s["N"]
+    assert gg.compact_rows == sum(gg.pair_rays(i, j) for i in range(M) for j in range(N))
+    assert gg.compact_rows <= frac * N * gg.n_rows

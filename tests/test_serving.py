@@ -41,9 +41,16 @@ def test_request_bytes_model():
     bf = B.bsgd_request_bytes(g, 4, 4, params(B.BF16))
     R = 90 * 64 * 64
     C = 64 ** 3
-    # the state holds y, r, z^j and r~^j (2 + 2N sinograms) plus the image, g, ...
-    assert f32 >= (2 + 2 * 4) * R * 4 + 3 * C * 4
+    # the state holds y, r (two sinograms), z^j and r~^j for each block's band
+    # (compact storage: less than the 2 N full sinograms), the image, g, ...
+    assert f32 >= 2 * R * 4 + 3 * C * 4
     assert bf < f32
+    # compact storage: doubling the column blocks adds far less than the 2 x 4
+    # extra full sinograms (one pair per iteration in both cases)
+    one = dict(alpha=1 / 4, epochs=2, rho=0.25, power_iters=10)
+    f4 = B.bsgd_request_bytes(g, 4, 4, B.SolveParams(gamma=1 / 4, **one))
+    f8 = B.bsgd_request_bytes(g, 4, 8, B.SolveParams(gamma=1 / 8, **one))
+    assert f8 - f4 < 0.5 * (2 * 4 * R * 4)
     # growing the problem grows the bill
     assert B.bsgd_request_bytes(cone(128, 180), 4, 4, params()) > 4 * f32 / 2
 
