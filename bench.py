@@ -330,7 +330,9 @@ def run_cuda(args):
             "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (state 1.9 GB; one iteration touches ~150 MB)",
-                       "mu": mu, "residual_norm_end": q1["residual_norm"]},
+                       "mu": mu, "residual_norm_end": q1["residual_norm"],
+                       "compact_rows_frac": round(gg.compact_rows / (N * gg.n_rows), 4),
+                       "state_gb": round(B.bsgd_request_bytes(GEOM, M, N, prm) / 1e9, 3)},
             "gpu_launches": int(launches), "stages_ms": stages,
             "kernels": "split FP / BP" if args.split else "fused FP+residual+BP",
             "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
