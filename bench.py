@@ -307,6 +307,9 @@ def run_cuda(args):
     if not args.no_extra and rank == 0 and world == 1:
         extra = extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks)
 
+    if extra is not None:
+        extra["P_precision_config"] = precision_leg(B, torch, dev)
+
     paper = None
     if args.paper_scale != "off" and rank == 0 and world == 1:
         paper = paper_scale_leg(B, torch, dev, [c for c in args.paper_scale.split(",") if c])
@@ -436,6 +439,54 @@ def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks):
                          "value": round(2 * per_vol * AUTOGRAD_BATCH / (ms_ag * 1e-3) / 1e9, 3),
                          "unit": UNIT}
     ga.close()
+    return out
+
+
+# Precision configuration: 512^3 (0.5 mm), 720 views over 360 deg, 512^2
+# detector of 0.8 mm, DSO 500 / DSD 1000, M = N = 16 (alpha = gamma = 1/16, an
+# epoch of 256 iterations), TV lambda = 1e-3 with 20 FGP iterations once per
+# epoch, noise-free projections; BF16 storage of y, x, z^j, r, r~^j with FP32
+# arithmetic, against the same run with FP32 storage.
+PRECISION_GEOM = dict(kind="cone3d", nx=512, ny=512, nz=512, dx=0.5, dy=0.5, dz=0.5, n_views=720,
+                      nu=512, nv=512, du=0.8, dv=0.8, dso=500.0, dsd=1000.0)
+
+
+def precision_leg(B, torch, dev, epochs=2):
+    from paper_1903_11874_gb300 import synth
+    gg = B.Geometry(M=16, N=16, **PRECISION_GEOM)
+    vol = torch.from_numpy(synth.ellipsoid_phantom(256, 256, 256, 10, seed=0) * KAPPA).to(dev)
+    vol = vol.repeat_interleave(2, 0).repeat_interleave(2, 1).repeat_interleave(2, 2)
+    y = torch.zeros(gg.n_rows, device=dev)
+    B.bsgd_forward_project(gg, vol.reshape(-1).contiguous(), y)
+    lam = None
+    out = {"volume": "512^3 (0.5 mm)", "views": 720, "detector": "512^2 (0.8 mm)",
+           "blocks": "M=N=16, alpha=gamma=1/16", "tv": "lambda 1e-3, 20 FGP iterations per epoch"}
+    xs = {}
+    for name, storage, tdt in (("fp32", B.F32, torch.float32), ("bf16", B.BF16, torch.bfloat16)):
+        prm = B.SolveParams(alpha=1 / 16, gamma=1 / 16, step_rule=B.STEP_STRIP if lam is None else B.STEP_FIXED,
+                            rho=RHO, power_iters=5, mu=lam or 0.0, pair_sampling=B.PAIRS_UNIFORM,
+                            tv_lambda=1e-3, tv_iters=20, storage=storage, seed=1)
+        st = B.State(gg, prm, y)
+        lam = st.query()["mu"]            # the same step for both runs
+        x = torch.zeros(gg.n_cols, device=dev, dtype=tdt)
+        st.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(epochs):
+            st.block_step(x, 256)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / epochs
+        prof = st.read_profile()
+        q = st.query()
+        xs[name] = x.float()
+        out[name] = {"ms_per_epoch": round(ms, 2), "value": round(q["updates"] / epochs / (ms * 1e-3) / 1e9, 3),
+                     "unit": UNIT, "tv_ms_per_epoch": round(prof["tv"]["ms"] / epochs, 2),
+                     "residual_norm": q["residual_norm"]}
+        st.close()
+    d = float(torch.linalg.vector_norm(xs["bf16"] - xs["fp32"]) / torch.linalg.vector_norm(xs["fp32"]))
+    out["bf16_vs_fp32_rel_l2"] = round(d, 6)
+    out["mu"] = lam
     return out
 
 
