@@ -265,6 +265,10 @@ typedef struct {
     double auto_eps;         /* > 0 (the paper's epsilon)                            */
     double auto_delta;       /* in (0, 1) (the paper's delta; 0.4 in Sec. 5)          */
     double auto_t1, auto_t2; /* cosine thresholds t_1 > 0, t_2 (Algorithm 3)          */
+    /* bsgd_solve: run the last final_uniform_epochs epochs without importance
+     * sampling (uniform pairs, whole views), as suggested after Algorithm 2 to
+     * remove the sampling's bias from the last iterations (0: off). */
+    int final_uniform_epochs;
 } bsgd_solve_params;
 
 typedef struct {
@@ -353,6 +357,19 @@ typedef struct {
 } bsgd_profile;
 
 bsgd_status bsgd_state_profile(bsgd_state *s, int enable);
+/*
+ * Change how the next iterations draw their blocks (Algorithm 1 / 2): pair
+ * sampling (bsgd_pair_sampling) and sub-detector cells (bsgd_cell_sampling,
+ * n_cells as in bsgd_solve_params). The memory of every (block, cell) is kept,
+ * so switching from BSGD-IM to whole views continues the same SAG estimate.
+ * Iterations already launched are unaffected. May compute the geometry's
+ * tables for the new cell count (synchronises `stream` then).
+ * Errors: INVALID_ARG (residual pairs with more than one pair per iteration,
+ * bad mode or cell count).
+ */
+bsgd_status bsgd_state_set_sampling(bsgd_state *s, int pair_sampling, int cells, int n_cells,
+                                    void *stream);
+
 /* split = 1: run FP and BP as two kernels even with one column block per
  * iteration (to time them apart); default 0 (one fused kernel). */
 bsgd_status bsgd_state_set_split(bsgd_state *s, int split);

@@ -27,7 +27,7 @@ EXPORTS = (
     "bsgd_count_updates_noalloc", "bsgd_power_iteration", "bsgd_tv_prox", "bsgd_state_create", "bsgd_state_destroy",
     "bsgd_block_step", "bsgd_state_query", "bsgd_trace_stride", "bsgd_state_read_trace",
     "bsgd_state_set_replay", "bsgd_state_profile", "bsgd_state_read_profile",
-    "bsgd_state_set_split", "bsgd_solve",
+    "bsgd_state_set_split", "bsgd_state_set_sampling", "bsgd_solve",
     "bsgd_request_bytes", "bsgd_server_create", "bsgd_server_destroy", "bsgd_server_submit",
     "bsgd_server_wait", "bsgd_server_poll", "bsgd_server_get_stats",
 )
@@ -76,6 +76,7 @@ class SolveParamsC(ctypes.Structure):
         ("storage", ctypes.c_int), ("seed", ctypes.c_uint64),
         ("auto_mu", ctypes.c_int), ("auto_window", ctypes.c_int), ("auto_eps", ctypes.c_double),
         ("auto_delta", ctypes.c_double), ("auto_t1", ctypes.c_double), ("auto_t2", ctypes.c_double),
+        ("final_uniform_epochs", ctypes.c_int),
     ]
 
 
@@ -157,6 +158,7 @@ def load(build_if_missing: bool = True):
         "bsgd_state_set_replay": (st, [_vp, _i32p, ctypes.c_int64]),
         "bsgd_state_profile": (st, [_vp, ctypes.c_int]),
         "bsgd_state_set_split": (st, [_vp, ctypes.c_int]),
+        "bsgd_state_set_sampling": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
         "bsgd_state_read_profile": (st, [_vp, P(Profile), _vp]),
         "bsgd_solve": (st, [_vp, P(SolveParamsC), _vp, st, _vp, st, P(Report), _vp]),
         "bsgd_request_bytes": (st, [P(GeometryDesc), ctypes.c_int, ctypes.c_int, P(SolveParamsC),
@@ -383,13 +385,16 @@ class SolveParams:
     auto_delta: float = 0.4
     auto_t1: float = 0.2
     auto_t2: float = 0.5
+    # bsgd_solve: last epochs without importance sampling (after Algorithm 2)
+    final_uniform_epochs: int = 0
 
     def c(self):
         return SolveParamsC(self.alpha, self.gamma, self.epochs, self.step_rule, self.mu, self.rho,
                             self.power_iters, self.pair_sampling, self.cells, self.n_cells,
                             self.tv_lambda, self.tv_iters, self.storage, self.seed,
                             int(bool(self.auto_mu)), self.auto_window, self.auto_eps,
-                            self.auto_delta, self.auto_t1, self.auto_t2)
+                            self.auto_delta, self.auto_t1, self.auto_t2,
+                            int(self.final_uniform_epochs))
 
 
 class State:
@@ -430,6 +435,10 @@ class State:
 
     def profile(self, enable=True):
         _check(load().bsgd_state_profile(self.handle, int(bool(enable))))
+
+    def set_sampling(self, pair_sampling, cells=0, n_cells=1, stream=None):
+        _check(load().bsgd_state_set_sampling(self.handle, int(pair_sampling), int(cells),
+                                              int(n_cells), _stream(stream)))
 
     def set_split(self, split=True):
         _check(load().bsgd_state_set_split(self.handle, int(bool(split))))

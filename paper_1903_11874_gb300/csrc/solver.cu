@@ -1392,6 +1392,32 @@ extern "C" bsgd_status bsgd_state_profile(bsgd_state *s, int enable) {
     return BSGD_OK;
 }
 
+extern "C" bsgd_status bsgd_state_set_sampling(bsgd_state *s, int pair_sampling, int cells,
+                                               int n_cells, void *stream) {
+    if (!s) return fail(BSGD_ERR_INVALID_ARG, "state is NULL");
+    const bsgd_geometry *g = s->g;
+    if (pair_sampling != BSGD_PAIRS_UNIFORM && pair_sampling != BSGD_PAIRS_RESIDUAL)
+        return fail(BSGD_ERR_INVALID_ARG, "bad pair sampling");
+    if (pair_sampling == BSGD_PAIRS_RESIDUAL && (s->P != 1 || g->M * g->N > kMaxResidualPairs))
+        return fail(BSGD_ERR_INVALID_ARG, "residual pair sampling draws one pair per iteration");
+    if (cells < BSGD_CELLS_NONE || cells > BSGD_CELLS_UNIFORM)
+        return fail(BSGD_ERR_INVALID_ARG, "bad cell sampling");
+    if (cells != BSGD_CELLS_NONE && n_cells != (g->desc.nv > 1 ? 4 : 2))
+        return fail(BSGD_ERR_INVALID_ARG, "n_cells must be 4 (3D) or 2 (2D)");
+    const int nc = cells == BSGD_CELLS_NONE ? 1 : n_cells;
+    unsigned long long *counts = nullptr;
+    double *cw = nullptr;
+    BSGD_TRY(geometry_tables(g, nc, cells == BSGD_CELLS_GEOMETRIC, (cudaStream_t)stream, &counts, &cw));
+    s->p.pair_sampling = pair_sampling;
+    s->p.cells = cells;
+    s->p.n_cells = nc;
+    s->n_cells = nc;
+    s->counts = counts;
+    s->cw = cw;
+    s->dev.n_cells = nc;
+    return BSGD_OK;
+}
+
 extern "C" bsgd_status bsgd_state_set_split(bsgd_state *s, int split) {
     if (!s) return fail(BSGD_ERR_INVALID_ARG, "state is NULL");
     s->split = split != 0;
@@ -1487,7 +1513,12 @@ extern "C" bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_param
         const bsgd_dtype sd = (bsgd_dtype)p->storage;
         BSGD_TRY(palloc(&xs, C * dtype_size(sd), st));
         BSGD_CUDA(cudaMemsetAsync(xs, 0, C * dtype_size(sd), st));
-        BSGD_TRY(bsgd_block_step(s, xs, p->epochs * s->epoch_len, stream));
+        const int fin = std::max(0, std::min(p->final_uniform_epochs, p->epochs));
+        BSGD_TRY(bsgd_block_step(s, xs, (p->epochs - fin) * s->epoch_len, stream));
+        if (fin > 0) {   // last epochs without importance sampling (after Algorithm 2)
+            BSGD_TRY(bsgd_state_set_sampling(s, BSGD_PAIRS_UNIFORM, BSGD_CELLS_NONE, 1, stream));
+            BSGD_TRY(bsgd_block_step(s, xs, fin * s->epoch_len, stream));
+        }
         void *xo = x;
         if (xh) {
             BSGD_TRY(palloc(&dx, C * dtype_size(xt), st));

@@ -263,3 +263,52 @@ def test_compact_band_storage(name, frac):
     M, N = s["M"], s["N"]
     assert gg.compact_rows == sum(gg.pair_rays(i, j) for i in range(M) for j in range(N))
     assert gg.compact_rows <= frac * N * gg.n_rows
+
+
+def test_switch_to_whole_views_matches_oracle():
+    """BSGD-IM (geometric cells, uniform pairs) for two epochs, then the
+    iterations after Algorithm 2's suggestion: whole views, uniform pairs. The
+    cell memories carry over (snapshot form), so the oracle replays the GPU's
+    cells for the first phase and samples whole views for the second."""
+    s, og, gg, y, mu, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    k1, k2 = 32, 32
+    prm = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu, seed=6,
+                        pair_sampling=B.PAIRS_UNIFORM, cells=B.CELLS_GEOMETRIC, n_cells=4)
+    st = B.State(gg, prm, torch.from_numpy(y.astype(np.float32)).to(DEV))
+    x = torch.zeros(gg.n_cols, device=DEV)
+    st.block_step(x, k1)
+    st.set_sampling(B.PAIRS_UNIFORM, B.CELLS_NONE)
+    st.block_step(x, k2)
+    torch.cuda.synchronize()
+    tr = st.read_trace(k1 + k2)
+    assert (tr[k1:, 3:] == -1).all()                     # no cells after the switch
+    po = OB.Params(M, N, 1 / M, 1 / N, mu, seed=6, cells="geometric", n_cells=4)
+    ost = OB.BSGDState(og, y, po)
+    for sel in oracle_replay(tr[:k1], 1, gg.info.max_views_per_block, M, og, po, True):
+        ost.step(sel)
+    import dataclasses
+    ost.prm = dataclasses.replace(po, cells="none", n_cells=1)
+    for _ in range(k2):
+        ost.step()
+    assert [h.pairs for h in ost.history[k1:]] == [
+        [(int(t[1]), int(t[2]))] for t in tr[k1:]]
+    assert rel_l2(x.cpu().double().numpy(), ost.x) <= 1e-5
+
+
+def test_solve_final_uniform_epochs_equals_manual_switch():
+    s, og, gg, y, mu, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    kw = dict(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu, seed=8,
+              pair_sampling=B.PAIRS_RESIDUAL, cells=B.CELLS_GEOMETRIC, n_cells=4)
+    xh = np.zeros(gg.n_cols, dtype=np.float32)
+    B.bsgd_solve(gg, B.SolveParams(epochs=3, final_uniform_epochs=1, **kw), y.astype(np.float32), xh)
+    st = B.State(gg, B.SolveParams(**kw), torch.from_numpy(y.astype(np.float32)).to(DEV))
+    x = torch.zeros(gg.n_cols, device=DEV)
+    st.block_step(x, 2 * M * N)
+    st.set_sampling(B.PAIRS_UNIFORM, B.CELLS_NONE)
+    st.block_step(x, M * N)
+    assert rel_l2(xh, x.cpu().double().numpy()) <= 1e-5
+    with pytest.raises(B.BSGDError):
+        B.State(gg, B.SolveParams(alpha=2 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu),
+                torch.from_numpy(y.astype(np.float32)).to(DEV)).set_sampling(B.PAIRS_RESIDUAL, B.CELLS_NONE)
