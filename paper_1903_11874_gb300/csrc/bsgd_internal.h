@@ -254,6 +254,7 @@ struct SampleArgs {
     Work *work;
     int *cells;                 // kMaxPairs x max_views
     int64_t *iter;
+    int64_t it;                 // the iteration, when the launcher knows it (else -1: read *iter)
     uint64_t seed;
     int pairs_mode, cells_mode, n_cells, kM, kN;
     const double *S;            // M x nv

@@ -57,8 +57,8 @@ __device__ inline int pick_weighted(double u, const double *w, int n, int stride
 
 constexpr int kSampleThreads = 256;
 constexpr int kMaxSampleBlocks = 1024;
-constexpr int kSampleSmemS = 2048;     // FP64 residual table entries staged in shared memory
-constexpr int kMaxResidualPairs = 2048;
+constexpr int kMaxResidualPairs = 1024;
+constexpr int kSampleSmemS = 2048;     // residual-table entries staged in shared memory
 
 // One iteration's draw (Algorithm 1's selection step; Algorithm 2's per-view
 // cells), executed by one CTA of kSampleThreads threads. Writes the work list,
@@ -66,8 +66,10 @@ constexpr int kMaxResidualPairs = 2048;
 // iteration counter.
 __device__ void sample_body(const SampleArgs &A) {
     // one buffer, two uses: the uniform draw's permutations, or the residual
-    // table and the pair weights
+    // table (staged with one parallel load: the draw is a latency chain) and
+    // the pair weights
     __shared__ double s_buf[kSampleSmemS + kMaxResidualPairs];
+    static_assert(2 * kMaxSampleBlocks * sizeof(int) <= sizeof(s_buf), "permutation buffers");
     int *s_rows = reinterpret_cast<int *>(s_buf);
     int *s_cols = s_rows + kMaxSampleBlocks;
     double *s_S = s_buf;
@@ -76,7 +78,7 @@ __device__ void sample_body(const SampleArgs &A) {
     __shared__ int s_pi[kMaxPairs], s_pj[kMaxPairs];
     __shared__ unsigned long long s_upd;
     const DeviceGeom &G = A.G;
-    const int64_t it = *A.iter;
+    const int64_t it = A.it >= 0 ? A.it : *A.iter;
     const int tid = threadIdx.x;
     const bool replay = A.replay && it >= A.replay_start && it - A.replay_start < A.replay_n;
     const int32_t *rep = replay ? A.replay + (it - A.replay_start) * A.stride : nullptr;
@@ -236,7 +238,7 @@ __device__ void sample_body(const SampleArgs &A) {
         }
         W.n_cols = nc;
         W.n_rows = nr;
-        *A.updates += 2ull * s_upd;
+        atomicAdd(A.updates, 2ull * s_upd);
         if (A.trace && it < A.trace_cap) {
             int32_t *t = A.trace + it * A.stride;
             t[0] = np;
@@ -399,6 +401,19 @@ __device__ void update_body(const DeviceGeom &G, const SolveDev &S, T *__restric
             if (full || (x0 + k < nx && y0 + lane < ny)) stf(xT + bT + k * ny + lane, sx[lane][k]);
         }
     }
+}
+
+// The block update of this iteration (every CTA but the last row) and the
+// draw of the next iteration (the first CTA of the last row).
+template <typename T>
+__global__ void __launch_bounds__(256) update_sample_kernel(const DeviceGeom G, const SolveDev S,
+                                                            T *__restrict__ x, T *__restrict__ xlo,
+                                                            const SampleArgs An) {
+    if (blockIdx.y == gridDim.y - 1) {
+        if (blockIdx.x == 0) sample_body(An);
+        return;
+    }
+    update_body<T>(G, S, x, xlo, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // xT = transpose(x) over the whole volume (y fastest), through shared memory.
@@ -938,7 +953,7 @@ static bsgd_status check_params(const bsgd_geometry *g, const bsgd_solve_params 
     if (g->M > kMaxSampleBlocks || g->N > kMaxSampleBlocks || g->M > 64)
         return fail(BSGD_ERR_INVALID_ARG, "the solver supports M <= 64 and N <= 1024");
     if (p->pair_sampling == BSGD_PAIRS_RESIDUAL && g->M * g->N > kMaxResidualPairs)
-        return fail(BSGD_ERR_INVALID_ARG, "residual sampling supports M * N <= 2048");
+        return fail(BSGD_ERR_INVALID_ARG, "residual sampling supports M * N <= 1024");
     if (p->tv_lambda < 0 || (p->tv_lambda > 0 && p->tv_iters < 1))
         return fail(BSGD_ERR_INVALID_ARG, "tv_lambda >= 0 and tv_iters >= 1");
     if (p->tv_lambda > 0 && g->desc.nz > 65535)
@@ -1057,8 +1072,8 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     if ((e = palloc(&s->y, R * es, st)) || (e = palloc(&s->z, (size_t)Z * es, st)) ||
         (e = palloc(&s->rt, (size_t)Z * es, st)) || (e = palloc(&s->r, R * es, st)) ||
         (e = palloc((void **)&s->grad, C * 4, st)) || (e = palloc((void **)&s->S, 8 * (size_t)M * g->desc.nv, st)) ||
-        (e = palloc((void **)&s->d_mu, 8, st)) || (e = palloc((void **)&s->work, sizeof(Work), st)) ||
-        (e = palloc((void **)&s->cells, 4 * (size_t)kMaxPairs * g->max_views, st)) ||
+        (e = palloc((void **)&s->d_mu, 8, st)) || (e = palloc((void **)&s->work, 2 * sizeof(Work), st)) ||
+        (e = palloc((void **)&s->cells, 2 * 4 * (size_t)kMaxPairs * g->max_views, st)) ||
         (e = palloc((void **)&s->wband, 4 * g->wband.size(), st)) ||
         (e = palloc((void **)&s->d_iter, 8, st)) ||
         (e = palloc((void **)&s->trace, 4 * (size_t)s->trace_cap * s->stride, st)) ||
@@ -1086,8 +1101,8 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         if (s->gT) BSGD_CUDA(cudaMemsetAsync(s->gT, 0, C * 4, st));
         BSGD_CUDA(cudaMemsetAsync(s->d_iter, 0, 8, st));
         BSGD_CUDA(cudaMemsetAsync(s->updates, 0, 8, st));
-        BSGD_CUDA(cudaMemsetAsync(s->work, 0, sizeof(Work), st));
-        BSGD_CUDA(cudaMemsetAsync(s->cells, 0xff, 4 * (size_t)kMaxPairs * g->max_views, st));
+        BSGD_CUDA(cudaMemsetAsync(s->work, 0, 2 * sizeof(Work), st));
+        BSGD_CUDA(cudaMemsetAsync(s->cells, 0xff, 2 * 4 * (size_t)kMaxPairs * g->max_views, st));
         BSGD_CUDA(cudaMemcpyAsync(s->wband, g->wband.data(), 4 * g->wband.size(),
                                   cudaMemcpyHostToDevice, st));
         BSGD_TRY(norm_table(g, s->r, s->st, s->S, st));
@@ -1178,12 +1193,21 @@ extern "C" bsgd_status bsgd_state_destroy(bsgd_state *s) {
     return BSGD_OK;
 }
 
-static void fill_sample_args(const bsgd_state *s, SampleArgs &A) {
+// The work list and the chosen cells are double-buffered by iteration parity,
+// so the draw of iteration k + 1 can run while iteration k's update reads its
+// own list.
+static Work *work_buf(const bsgd_state *s, int64_t k) { return s->work + (k & 1); }
+static int *cells_buf(const bsgd_state *s, int64_t k) {
+    return s->cells + (k & 1) * (size_t)kMaxPairs * s->g->max_views;
+}
+
+static void fill_sample_args(const bsgd_state *s, SampleArgs &A, int64_t k) {
     const bsgd_geometry *g = s->g;
     A = SampleArgs{};
+    A.it = k;
     A.G = g->dg;
-    A.work = s->work;
-    A.cells = s->cells;
+    A.work = work_buf(s, k);
+    A.cells = cells_buf(s, k);
     A.iter = s->d_iter;
     A.seed = s->p.seed;
     A.pairs_mode = s->p.pair_sampling;
@@ -1214,7 +1238,10 @@ bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out) {
     ReqDesc d{};
     d.G = g->dg;
     d.S = s->dev;
-    fill_sample_args(s, d.A);
+    d.S.work = work_buf(s, 0);   // served rounds draw, solve and update in one buffer
+    d.S.cells = cells_buf(s, 0);
+    fill_sample_args(s, d.A, 0);
+    d.A.it = -1;                 // served rounds count iterations on the device
     d.x = x;
     d.xlo = s->xlo;
     d.dtype = s->st;
@@ -1285,14 +1312,24 @@ static bsgd_status sync_xT(bsgd_state *s, void *x, cudaStream_t st) {
     return BSGD_OK;
 }
 
-static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
+// One iteration. `drawn`: its blocks were drawn by the previous iteration's
+// update launch; `draw_next`: this iteration's update launch also draws the
+// next iteration's blocks.
+static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st, bool drawn,
+                                 bool draw_next) {
     const bsgd_geometry *g = s->g;
-    SampleArgs A;
-    fill_sample_args(s, A);
-    cudaEvent_t b = stage_begin(s, st);
-    sample_kernel<<<1, kSampleThreads, 0, st>>>(A);
-    BSGD_CUDA(cudaGetLastError());
-    stage_end(s, BSGD_STAGE_SAMPLE, b, 1, st);
+    const int64_t k = s->iters;
+    s->dev.work = work_buf(s, k);
+    s->dev.cells = cells_buf(s, k);
+    cudaEvent_t b = nullptr;
+    if (!drawn) {
+        SampleArgs A;
+        fill_sample_args(s, A, k);
+        b = stage_begin(s, st);
+        sample_kernel<<<1, kSampleThreads, 0, st>>>(A);
+        BSGD_CUDA(cudaGetLastError());
+        stage_end(s, BSGD_STAGE_SAMPLE, b, 1, st);
+    }
     if (s->max_tiles > 0 && s->fused && !s->split) {
         // one column block per iteration: FP, residual and BP in one pass
         b = stage_begin(s, st);
@@ -1323,9 +1360,23 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st) {
                              : (maxJ + 1023) / 1024;
     dim3 ug((unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, 65535)), s->kN);
     b = stage_begin(s, st);
-    if (s->st == BSGD_F32) update_kernel<float><<<ug, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr);
-    else if (s->st == BSGD_BF16) update_kernel<__nv_bfloat16><<<ug, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo);
-    else update_kernel<__half><<<ug, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo);
+    if (draw_next) {
+        // the draw of iteration k + 1 needs only the residual table, final
+        // once this iteration's FPs are done: one extra CTA of the update
+        SampleArgs An;
+        fill_sample_args(s, An, k + 1);
+        dim3 ugs(ug.x, ug.y + 1);
+        if (s->st == BSGD_F32)
+            update_sample_kernel<float><<<ugs, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr, An);
+        else if (s->st == BSGD_BF16)
+            update_sample_kernel<__nv_bfloat16><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo, An);
+        else
+            update_sample_kernel<__half><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo, An);
+    } else {
+        if (s->st == BSGD_F32) update_kernel<float><<<ug, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr);
+        else if (s->st == BSGD_BF16) update_kernel<__nv_bfloat16><<<ug, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo);
+        else update_kernel<__half><<<ug, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo);
+    }
     BSGD_CUDA(cudaGetLastError());
     stage_end(s, BSGD_STAGE_UPDATE, b, 1, st);
     s->iters += 1;
@@ -1355,7 +1406,7 @@ extern "C" bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void
     if (n_iters < 0) return fail(BSGD_ERR_INVALID_ARG, "n_iters < 0");
     cudaStream_t st = (cudaStream_t)stream;
     if (n_iters > 0) BSGD_TRY(sync_xT(s, x, st));
-    for (int k = 0; k < n_iters; ++k) BSGD_TRY(one_iteration(s, x, st));
+    for (int k = 0; k < n_iters; ++k) BSGD_TRY(one_iteration(s, x, st, k > 0, k + 1 < n_iters));
     return BSGD_OK;
 }
 

@@ -91,10 +91,13 @@ def test_results_alone_equal_results_in_the_mix():
     try:
         ida = srv.submit(geoA, 4, 4, pA, yA)
         x_alone, rep_alone = srv.wait(ida)
-        # B runs long enough for A and C to be admitted while it is resident
-        ids = [srv.submit(geoB, 4, 4, params(seed=6, epochs=40), yB),
-               srv.submit(geoA, 4, 4, pA, yA),
-               srv.submit(geoC, 4, 4, params(B.BF16, seed=7), yC)]
+        # B is resident before A and C are submitted, and runs long enough
+        # (400 epochs) for both to be admitted while it still runs
+        idb = srv.submit(geoB, 4, 4, params(seed=6, epochs=400), yB)
+        t0 = time.time()
+        while srv.stats()["resident"] < 1 and srv.stats()["completed"] < 2 and time.time() - t0 < 60:
+            time.sleep(0.001)
+        ids = [idb, srv.submit(geoA, 4, 4, pA, yA), srv.submit(geoC, 4, 4, params(B.BF16, seed=7), yC)]
         outs = [srv.wait(i) for i in ids]
         st = srv.stats()
     finally:
