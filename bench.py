@@ -105,6 +105,18 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def reduce_over_ranks(torch, dist, seconds, units, device):
+    """Whole-job figures of N replicas: the slowest rank's time and the units
+    all ranks processed (one rank: the values themselves)."""
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(seconds), float(units)
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    u = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -238,14 +250,7 @@ def run_cuda(args):
     prof = st.read_profile()
     q1 = st.query()
     updates = q1["updates"] - q0["updates"]
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        u = torch.tensor([float(updates)], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        ms, updates_all = float(t.item()), float(u.item())
-    else:
-        updates_all = float(updates)
+    ms, updates_all = reduce_over_ranks(torch, dist, ms, updates, dev)
     value = updates_all / (ms * 1e-3) / 1e9
 
     # ---- roofline of the dominant kernel (FP or BP), timed live above
@@ -293,12 +298,7 @@ def run_cuda(args):
             rep = B.bsgd_solve(gg, pe, yh, xh)
             upd_e2e += rep["updates"]
         t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            u = torch.tensor([float(upd_e2e)], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dist.all_reduce(u, op=dist.ReduceOp.SUM)
-            t_e2e, upd_e2e = float(t.item()), float(u.item())
+        t_e2e, upd_e2e = reduce_over_ranks(torch, dist, t_e2e, upd_e2e, dev)
         e2e = {"value": round(upd_e2e / t_e2e / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": int(gg.n_rows * 4), "d2h_bytes_per_step": int(gg.n_cols * 4),
                "api": "bsgd_solve (1 epoch per call, pinned host y and x, fixed mu)"}
