@@ -194,14 +194,17 @@ def make_inputs(B, gg, torch, dev, seed_offset=0):
 
 def algorithmic_bytes(gg, n_pairs_avg_rays, storage_bytes=4):
     """Compulsory DRAM bytes of one pair in the FP, BP and fused FP+BP kernels,
-    per the kernels' data flow: FP reads x_J and, per traced ray, y, every z^j
-    and r, and writes z^J and r; BP reads r and r~^J, writes r~^J and
-    read-modify-writes g_J; the fused kernel does both without re-reading r."""
+    per the kernels' data flow: FP reads x_J and, per traced ray, y, r and the
+    z^j of the blocks whose band holds the ray (compact band storage; on
+    average `nb` of them, from the geometry's band areas), and writes z^J and
+    r; BP reads r and r~^J, writes r~^J and read-modify-writes g_J; the fused
+    kernel does both without re-reading r."""
     vox_j = gg.n_cols // N
     rays = n_pairs_avg_rays
-    fp = vox_j * storage_bytes + rays * storage_bytes * (1 + N + 1 + 2)
+    nb = max(1.0, gg.compact_rows / gg.n_rows)
+    fp = vox_j * storage_bytes + rays * storage_bytes * (1 + nb + 1 + 2)
     bp = rays * storage_bytes * 3 + vox_j * 8
-    fpbp = vox_j * (storage_bytes + 8) + rays * storage_bytes * (N + 6)
+    fpbp = vox_j * (storage_bytes + 8) + rays * storage_bytes * (nb + 6)
     return {"fp": fp, "bp": bp, "fpbp": fpbp}
 
 
@@ -332,7 +335,8 @@ def run_cuda(args):
             "data": "synthetic (seeded ellipsoid phantom, Poisson noise)",
             "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (state 1.9 GB; one iteration touches ~150 MB)",
+                       "l2": "inputs larger than L2 (state ~0.8 GB resident; one iteration "
+                             "touches ~100 MB across launches of different slabs)",
                        "mu": mu, "residual_norm_end": q1["residual_norm"],
                        "compact_rows_frac": round(gg.compact_rows / (N * gg.n_rows), 4),
                        "state_gb": round(B.bsgd_request_bytes(GEOM, M, N, prm) / 1e9, 3)},
