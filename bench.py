@@ -421,6 +421,22 @@ def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks):
     ms_us = prof["update"]["ms"] / max(prof["update"]["launches"], 1)
     out["a2_a3_sample"] = {"ms_per_launch": round(ms_s, 4), "bound": "latency (one CTA)",
                            "update_with_next_draw_ms": round(ms_us, 4)}
+    # a8: the step size's FP64 power iteration, 30 steps (FP + BP) of one strip
+    j = 0
+    per_fp = B.bsgd_count_updates(gg, col_blocks=[j])
+    B.bsgd_power_iteration(gg, j, 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B.bsgd_power_iteration(gg, j, 30)
+    dt = time.perf_counter() - t0
+    out["a8_power_iteration"] = {"ms": round(dt * 1e3, 2), "iterations": 30,
+                                 "value": round(2 * 30 * per_fp / dt / 1e9, 3), "unit": UNIT,
+                                 "note": "one column strip, all views; FP64 vector state"}
+    # a1: geometry and band tables (host FP64, uploaded)
+    t0 = time.perf_counter()
+    g2 = B.Geometry(M=M, N=N, **GEOM)
+    out["a1_geometry_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+    g2.close()
     # P: the same workload with BF16 storage (FP32 arithmetic)
     prm16 = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu,
                           pair_sampling=B.PAIRS_RESIDUAL, storage=B.BF16, seed=1)
