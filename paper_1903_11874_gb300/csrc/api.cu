@@ -83,16 +83,29 @@ extern "C" bsgd_status bsgd_forward_project(const bsgd_geometry *g, const void *
     BSGD_TRY(block_lists(g, row_blocks, n_rb, col_blocks, n_cb, rows, runs));
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t C = g->n_cols(), R = g->n_rows();
-    for (int b = 0; b < batch; ++b) {
-        const char *xb = (const char *)x + (size_t)b * C * dtype_size(xt);
-        char *yb = (char *)y + (size_t)b * R * dtype_size(yt);
-        if (!accumulate) BSGD_TRY(zero_rows(g, rows.data(), (int)rows.size(), yb, yt, st));
-        for (auto &run : runs) {
-            PlainLaunch L{rows.data(), (int)rows.size(), run.first, run.second, 0};
-            BSGD_TRY(launch_fp_plain(g, L, xb, xt, yb, yt, 1, st));
+    // y-fastest copy of each image for the views whose rays run along x; the
+    // projection is the same without it (only slower), so a failed allocation
+    // is not an error
+    void *xT = nullptr;
+    if (plain_wants_transpose(g, rows.data(), (int)rows.size()) &&
+        pool_alloc(&xT, (size_t)C * dtype_size(xt), st) != BSGD_OK)
+        xT = nullptr;
+    auto run_all = [&]() -> bsgd_status {
+        for (int b = 0; b < batch; ++b) {
+            const char *xb = (const char *)x + (size_t)b * C * dtype_size(xt);
+            char *yb = (char *)y + (size_t)b * R * dtype_size(yt);
+            if (!accumulate) BSGD_TRY(zero_rows(g, rows.data(), (int)rows.size(), yb, yt, st));
+            for (auto &run : runs) {
+                if (xT) BSGD_TRY(plain_transpose(g, xb, xt, xT, run.first, run.second, st));
+                PlainLaunch L{rows.data(), (int)rows.size(), run.first, run.second, 0};
+                BSGD_TRY(launch_fp_plain(g, L, xb, xt, yb, yt, 1, st, xT));
+            }
         }
-    }
-    return BSGD_OK;
+        return BSGD_OK;
+    };
+    const bsgd_status s = run_all();
+    pool_free(xT, st);
+    return s;
 }
 
 extern "C" bsgd_status bsgd_back_project(const bsgd_geometry *g, const void *r, bsgd_dtype rt,
@@ -108,20 +121,31 @@ extern "C" bsgd_status bsgd_back_project(const bsgd_geometry *g, const void *r, 
     BSGD_TRY(block_lists(g, row_blocks, n_rb, col_blocks, n_cb, rows, runs));
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t C = g->n_cols(), R = g->n_rows();
-    for (int b = 0; b < batch; ++b) {
-        const char *rb = (const char *)r + (size_t)b * R * dtype_size(rt);
-        float *xb = (float *)x + (size_t)b * C;
-        for (auto &run : runs) {
-            if (!accumulate) {
+    // y-fastest FP32 accumulator for the views whose rays run along x, added
+    // back into x after each run (optional, as in the forward projection)
+    float *gT = nullptr;
+    if (plain_wants_transpose(g, rows.data(), (int)rows.size()) &&
+        pool_alloc((void **)&gT, (size_t)C * 4, st) != BSGD_OK)
+        gT = nullptr;
+    auto run_all = [&]() -> bsgd_status {
+        for (int b = 0; b < batch; ++b) {
+            const char *rb = (const char *)r + (size_t)b * R * dtype_size(rt);
+            float *xb = (float *)x + (size_t)b * C;
+            for (auto &run : runs) {
                 const int64_t v0 = (int64_t)g->plane_start[run.first] * g->dg.plane_stride;
                 const int64_t v1 = (int64_t)g->plane_start[run.second] * g->dg.plane_stride;
-                BSGD_CUDA(cudaMemsetAsync(xb + v0, 0, (v1 - v0) * 4, st));
+                if (!accumulate) BSGD_CUDA(cudaMemsetAsync(xb + v0, 0, (v1 - v0) * 4, st));
+                if (gT) BSGD_CUDA(cudaMemsetAsync(gT + v0, 0, (v1 - v0) * 4, st));
+                PlainLaunch L{rows.data(), (int)rows.size(), run.first, run.second, 0};
+                BSGD_TRY(launch_bp_plain(g, L, rb, rt, xb, scale, st, gT));
+                if (gT) BSGD_TRY(plain_add_transposed(g, gT, xb, run.first, run.second, st));
             }
-            PlainLaunch L{rows.data(), (int)rows.size(), run.first, run.second, 0};
-            BSGD_TRY(launch_bp_plain(g, L, rb, rt, xb, scale, st));
         }
-    }
-    return BSGD_OK;
+        return BSGD_OK;
+    };
+    const bsgd_status s = run_all();
+    pool_free(gT, st);
+    return s;
 }
 
 extern "C" bsgd_status bsgd_count_updates(const bsgd_geometry *g, const int32_t *row_blocks,

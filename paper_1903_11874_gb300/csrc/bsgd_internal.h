@@ -93,6 +93,7 @@ struct bsgd_geometry {
     std::vector<bsgd::Band> bands;              // n_views x (N + 1), traversal bands
     std::vector<int> wband;                     // M x N x 2: exact v-band of the pair
     std::vector<int64_t> zoff;                  // N x n_views: compact band offsets
+    std::vector<unsigned char> view_yfast;      // host copy of dg.view_yfast
     int64_t zlen = 0;
     int device = 0;
     // device copies
@@ -142,11 +143,25 @@ struct PlainLaunch {
 int tiles_for(const bsgd_geometry *g, const std::vector<int> &views, int j0, int j1, int tile_u,
               int tile_v);
 
+// xT (optional): y-fastest copy of x over the launch's planes, gathered by the
+// views whose rays run along x; gT (optional): y-fastest FP32 accumulator that
+// those views scatter into instead of x (the caller adds it back with
+// plain_add_transposed).
 bsgd_status launch_fp_plain(const bsgd_geometry *g, const PlainLaunch &L, const void *x,
                             bsgd_dtype xt, void *y, bsgd_dtype yt, int accumulate,
-                            cudaStream_t st);
+                            cudaStream_t st, const void *xT = nullptr);
 bsgd_status launch_bp_plain(const bsgd_geometry *g, const PlainLaunch &L, const void *r,
-                            bsgd_dtype rt, float *x, float scale, cudaStream_t st);
+                            bsgd_dtype rt, float *x, float scale, cudaStream_t st,
+                            float *gT = nullptr);
+// True if a y-fastest copy pays for the listed row blocks: a volume with at
+// least one view whose rays run along x.
+bool plain_wants_transpose(const bsgd_geometry *g, const int *row_ids, int n_rb);
+// xT[z][x][y] = x[z][y][x] over the planes of column blocks [j0, j1).
+bsgd_status plain_transpose(const bsgd_geometry *g, const void *x, bsgd_dtype xt, void *xT, int j0,
+                            int j1, cudaStream_t st);
+// x[z][y][x] += gT[z][x][y] over the planes of column blocks [j0, j1).
+bsgd_status plain_add_transposed(const bsgd_geometry *g, const float *gT, float *x, int j0, int j1,
+                                 cudaStream_t st);
 bsgd_status launch_count(const bsgd_geometry *g, const PlainLaunch &L,
                          unsigned long long *d_count, cudaStream_t st);
 // Clear the rows of every view of the listed row blocks.

@@ -367,6 +367,7 @@ extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int 
     std::vector<unsigned char> yfast(d.n_views, 0);
     for (int a = 0; a < d.n_views && d.nz > 1; ++a)
         yfast[a] = std::fabs(std::cos(g->angles[a])) > std::fabs(std::sin(g->angles[a])) ? 1 : 0;
+    g->view_yfast = yfast;
     bsgd_status st = BSGD_OK;
     int dev = 0;
     cudaGetDevice(&dev);

@@ -28,29 +28,37 @@ __device__ __forceinline__ int sel_view(const DeviceGeom &G, const RowSel &R, in
 // ---------------------------------------------------------------------------
 // Plain kernels
 
+// Views whose rays run along x gather from xT (y fastest) when it is given, so
+// that the lanes of a warp (neighbouring detector columns) read neighbouring
+// addresses; the other views read x.
 template <bool k3D, typename TX, typename TY>
 __global__ void __launch_bounds__(128) fp_plain_kernel(const DeviceGeom G, const RowSel R, int j0,
                                                        int j1, const TX *__restrict__ x,
-                                                       TY *__restrict__ y) {
+                                                       TY *__restrict__ y,
+                                                       const TX *__restrict__ xT) {
     const int a = sel_view(G, R, blockIdx.y);
     if (a < 0) return;
     const Band b = band_of(G, a, j0, j1);
     int u, v, nt;
     if (!tile_pixel<k3D>(b, blockIdx.x, u, v, nt)) return;
+    const bool yf = xT != nullptr && G.view_yfast[a];
+    const TX *src = yf ? xT : x;
     RayWalk w;
     float acc = 0.f;
-    if (ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w)) {
-        ray_walk_fast(w, [&](int idx, float s) { acc = fmaf(s, ldf(x + idx), acc); });
+    if (ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w, yf)) {
+        ray_walk_fast(w, [&](int idx, float s) { acc = fmaf(s, ldf(src + idx), acc); });
         acc *= w.L;
     }
     const int64_t row = ((int64_t)a * G.nv + v) * G.nu + u;
     stf(y + row, ldv(y + row) + acc);
 }
 
+// Views whose rays run along x scatter into gT (y fastest) when it is given.
 template <bool k3D, typename TR>
 __global__ void __launch_bounds__(128) bp_plain_kernel(const DeviceGeom G, const RowSel R, int j0,
                                                        int j1, const TR *__restrict__ r,
-                                                       float *__restrict__ x, float scale) {
+                                                       float *__restrict__ x, float scale,
+                                                       float *__restrict__ gT) {
     const int a = sel_view(G, R, blockIdx.y);
     if (a < 0) return;
     const Band b = band_of(G, a, j0, j1);
@@ -59,12 +67,64 @@ __global__ void __launch_bounds__(128) bp_plain_kernel(const DeviceGeom G, const
     const int64_t row = ((int64_t)a * G.nv + v) * G.nu + u;
     const float rv = ldf(r + row) * scale;
     if (rv == 0.f) return;
+    const bool yf = gT != nullptr && G.view_yfast[a];
+    float *dst = yf ? gT : x;
     RayWalk w;
-    if (!ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w)) return;
+    if (!ray_setup(G, a, u, v, G.plane_start[j0], G.plane_start[j1], w, yf)) return;
     const float wl = rv * w.L;
     ray_walk_fast(w, [&](int idx, float s) {
-        if (s > 0.f) atomicAdd(x + idx, s * wl);
+        if (s > 0.f) atomicAdd(dst + idx, s * wl);
     });
+}
+
+// out[z][x][y] = in[z][y][x] for the planes z0 <= z < z1, through a 32 x 33
+// shared tile so that both the reads and the writes are coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_planes_kernel(const DeviceGeom G, int z0, int z1,
+                                                               const T *__restrict__ in,
+                                                               T *__restrict__ out) {
+    __shared__ float sx[32][33];
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int tx_n = (G.nx + 31) / 32, ty_n = (G.ny + 31) / 32;
+    const int64_t ntiles = (int64_t)tx_n * ty_n * (z1 - z0);
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int z = z0 + (int)(t / (tx_n * ty_n)), rem = (int)(t % (tx_n * ty_n));
+        const int x0 = (rem % tx_n) * 32, y0 = (rem / tx_n) * 32;
+        __syncthreads();
+        for (int k = row; k < 32; k += 8) {
+            const int yy = y0 + k, xx = x0 + lane;
+            if (xx < G.nx && yy < G.ny) sx[k][lane] = ldf(in + ((int64_t)z * G.ny + yy) * G.nx + xx);
+        }
+        __syncthreads();
+        for (int k = row; k < 32; k += 8) {
+            const int xx = x0 + k, yy = y0 + lane;
+            if (xx < G.nx && yy < G.ny) stf(out + ((int64_t)z * G.nx + xx) * G.ny + yy, sx[lane][k]);
+        }
+    }
+}
+
+// x[z][y][x] += gT[z][x][y] for the planes z0 <= z < z1.
+__global__ void __launch_bounds__(256) add_transposed_kernel(const DeviceGeom G, int z0, int z1,
+                                                             const float *__restrict__ gT,
+                                                             float *__restrict__ x) {
+    __shared__ float sg[32][33];
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int tx_n = (G.nx + 31) / 32, ty_n = (G.ny + 31) / 32;
+    const int64_t ntiles = (int64_t)tx_n * ty_n * (z1 - z0);
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int z = z0 + (int)(t / (tx_n * ty_n)), rem = (int)(t % (tx_n * ty_n));
+        const int x0 = (rem % tx_n) * 32, y0 = (rem / tx_n) * 32;
+        __syncthreads();
+        for (int k = row; k < 32; k += 8) {           // gT rows: fixed x, consecutive y
+            const int xx = x0 + k, yy = y0 + lane;
+            if (xx < G.nx && yy < G.ny) sg[k][lane] = gT[((int64_t)z * G.nx + xx) * G.ny + yy];
+        }
+        __syncthreads();
+        for (int k = row; k < 32; k += 8) {           // x rows: fixed y, consecutive x
+            const int yy = y0 + k, xx = x0 + lane;
+            if (xx < G.nx && yy < G.ny) x[((int64_t)z * G.ny + yy) * G.nx + xx] += sg[lane][k];
+        }
+    }
 }
 
 // Voxel-ray updates (segments longer than 1e-4 of the smallest voxel edge;
@@ -373,19 +433,28 @@ std::vector<int> views_of(const bsgd_geometry *g, const RowSel &R) {
 
 template <typename TX, typename TY>
 void fp_plain_go(const bsgd_geometry *g, dim3 grid, const RowSel &R, int j0, int j1, const void *x,
-                 void *y, cudaStream_t st) {
+                 void *y, const void *xT, cudaStream_t st) {
     if (g->desc.nv > 1)
-        fp_plain_kernel<true, TX, TY><<<grid, 128, 0, st>>>(g->dg, R, j0, j1, (const TX *)x, (TY *)y);
+        fp_plain_kernel<true, TX, TY><<<grid, 128, 0, st>>>(g->dg, R, j0, j1, (const TX *)x, (TY *)y,
+                                                            (const TX *)xT);
     else
-        fp_plain_kernel<false, TX, TY><<<grid, 128, 0, st>>>(g->dg, R, j0, j1, (const TX *)x, (TY *)y);
+        fp_plain_kernel<false, TX, TY><<<grid, 128, 0, st>>>(g->dg, R, j0, j1, (const TX *)x, (TY *)y,
+                                                             (const TX *)xT);
 }
 
 template <typename TX>
 void fp_plain_y(const bsgd_geometry *g, dim3 grid, const RowSel &R, int j0, int j1, const void *x,
-                void *y, bsgd_dtype yt, cudaStream_t st) {
-    if (yt == BSGD_F32) fp_plain_go<TX, float>(g, grid, R, j0, j1, x, y, st);
-    else if (yt == BSGD_BF16) fp_plain_go<TX, __nv_bfloat16>(g, grid, R, j0, j1, x, y, st);
-    else fp_plain_go<TX, __half>(g, grid, R, j0, j1, x, y, st);
+                void *y, bsgd_dtype yt, const void *xT, cudaStream_t st) {
+    if (yt == BSGD_F32) fp_plain_go<TX, float>(g, grid, R, j0, j1, x, y, xT, st);
+    else if (yt == BSGD_BF16) fp_plain_go<TX, __nv_bfloat16>(g, grid, R, j0, j1, x, y, xT, st);
+    else fp_plain_go<TX, __half>(g, grid, R, j0, j1, x, y, xT, st);
+}
+
+// Grid of the plane-tile kernels: 32 x 32 tiles over the planes, at most 16
+// CTAs of 256 threads per SM.
+int plane_tile_grid(const bsgd_geometry *g, int z0, int z1) {
+    const int64_t t = (int64_t)((g->desc.nx + 31) / 32) * ((g->desc.ny + 31) / 32) * (z1 - z0);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(t, 152 * 8));
 }
 
 }  // namespace
@@ -402,32 +471,65 @@ bsgd_status zero_rows(const bsgd_geometry *g, const int *row_ids, int n_rb, void
     });
 }
 
+bool plain_wants_transpose(const bsgd_geometry *g, const int *row_ids, int n_rb) {
+    if (g->desc.nz <= 1) return false;
+    for (int k = 0; k < n_rb; ++k)
+        for (int a : g->block_views[row_ids[k]])
+            if (g->view_yfast[a]) return true;
+    return false;
+}
+
+bsgd_status plain_transpose(const bsgd_geometry *g, const void *x, bsgd_dtype xt, void *xT, int j0,
+                            int j1, cudaStream_t st) {
+    const int z0 = g->plane_start[j0], z1 = g->plane_start[j1];
+    if (z1 <= z0) return BSGD_OK;
+    const int gb = plane_tile_grid(g, z0, z1);
+    if (xt == BSGD_F32)
+        transpose_planes_kernel<float><<<gb, 256, 0, st>>>(g->dg, z0, z1, (const float *)x, (float *)xT);
+    else if (xt == BSGD_BF16)
+        transpose_planes_kernel<__nv_bfloat16><<<gb, 256, 0, st>>>(
+            g->dg, z0, z1, (const __nv_bfloat16 *)x, (__nv_bfloat16 *)xT);
+    else
+        transpose_planes_kernel<__half><<<gb, 256, 0, st>>>(g->dg, z0, z1, (const __half *)x, (__half *)xT);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+bsgd_status plain_add_transposed(const bsgd_geometry *g, const float *gT, float *x, int j0, int j1,
+                                 cudaStream_t st) {
+    const int z0 = g->plane_start[j0], z1 = g->plane_start[j1];
+    if (z1 <= z0) return BSGD_OK;
+    add_transposed_kernel<<<plane_tile_grid(g, z0, z1), 256, 0, st>>>(g->dg, z0, z1, gT, x);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
 bsgd_status launch_fp_plain(const bsgd_geometry *g, const PlainLaunch &L, const void *x,
                             bsgd_dtype xt, void *y, bsgd_dtype yt, int accumulate,
-                            cudaStream_t st) {
+                            cudaStream_t st, const void *xT) {
     (void)accumulate;
     return for_row_chunks(g, L, [&](const RowSel &R) -> bsgd_status {
         const int tiles = tiles_for(g, views_of(g, R), L.j0, L.j1, tile_u(g), tile_v(g));
         if (tiles == 0) return BSGD_OK;
         dim3 grid(tiles, R.n * g->max_views);
-        if (xt == BSGD_F32) fp_plain_y<float>(g, grid, R, L.j0, L.j1, x, y, yt, st);
-        else if (xt == BSGD_BF16) fp_plain_y<__nv_bfloat16>(g, grid, R, L.j0, L.j1, x, y, yt, st);
-        else fp_plain_y<__half>(g, grid, R, L.j0, L.j1, x, y, yt, st);
+        if (xt == BSGD_F32) fp_plain_y<float>(g, grid, R, L.j0, L.j1, x, y, yt, xT, st);
+        else if (xt == BSGD_BF16) fp_plain_y<__nv_bfloat16>(g, grid, R, L.j0, L.j1, x, y, yt, xT, st);
+        else fp_plain_y<__half>(g, grid, R, L.j0, L.j1, x, y, yt, xT, st);
         BSGD_CUDA(cudaGetLastError());
         return BSGD_OK;
     });
 }
 
 bsgd_status launch_bp_plain(const bsgd_geometry *g, const PlainLaunch &L, const void *r,
-                            bsgd_dtype rt, float *x, float scale, cudaStream_t st) {
+                            bsgd_dtype rt, float *x, float scale, cudaStream_t st, float *gT) {
     return for_row_chunks(g, L, [&](const RowSel &R) -> bsgd_status {
         const int tiles = tiles_for(g, views_of(g, R), L.j0, L.j1, tile_u(g), tile_v(g));
         if (tiles == 0) return BSGD_OK;
         dim3 grid(tiles, R.n * g->max_views);
         const bool t3 = g->desc.nv > 1;
 #define BP_GO(T)                                                                                   \
-    if (t3) bp_plain_kernel<true, T><<<grid, 128, 0, st>>>(g->dg, R, L.j0, L.j1, (const T *)r, x, scale); \
-    else bp_plain_kernel<false, T><<<grid, 128, 0, st>>>(g->dg, R, L.j0, L.j1, (const T *)r, x, scale);
+    if (t3) bp_plain_kernel<true, T><<<grid, 128, 0, st>>>(g->dg, R, L.j0, L.j1, (const T *)r, x, scale, gT); \
+    else bp_plain_kernel<false, T><<<grid, 128, 0, st>>>(g->dg, R, L.j0, L.j1, (const T *)r, x, scale, gT);
         if (rt == BSGD_F32) { BP_GO(float) }
         else if (rt == BSGD_BF16) { BP_GO(__nv_bfloat16) }
         else { BP_GO(__half) }

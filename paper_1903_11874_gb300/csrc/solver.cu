@@ -873,15 +873,16 @@ bsgd_status power_iteration(const bsgd_geometry *g, int j, int iters, const int 
     const int64_t b0 = (int64_t)g->plane_start[j] * g->dg.plane_stride;
     const int64_t b1 = (int64_t)g->plane_start[j + 1] * g->dg.plane_stride;
     const int64_t n = g->n_cols(), m = g->n_rows();
-    float *v32 = nullptr, *w = nullptr, *y = nullptr;
+    float *v32 = nullptr, *w = nullptr, *y = nullptr, *vT = nullptr, *wT = nullptr;
     double *v64 = nullptr, *nrm = nullptr;
     bsgd_status s = BSGD_OK;
     auto cleanup = [&]() {
-        cudaFree(v32); cudaFree(w); cudaFree(y); cudaFree(v64); cudaFree(nrm);
+        for (void *p : {(void *)v32, (void *)w, (void *)y, (void *)v64, (void *)nrm, (void *)vT, (void *)wT})
+            pool_free(p, st);
     };
-    if ((s = dalloc((void **)&v32, n * 4)) || (s = dalloc((void **)&w, n * 4)) ||
-        (s = dalloc((void **)&y, m * 4)) || (s = dalloc((void **)&v64, (b1 - b0) * 8)) ||
-        (s = dalloc((void **)&nrm, 8 * (iters + 2)))) {
+    if ((s = palloc((void **)&v32, n * 4, st)) || (s = palloc((void **)&w, n * 4, st)) ||
+        (s = palloc((void **)&y, m * 4, st)) || (s = palloc((void **)&v64, (b1 - b0) * 8, st)) ||
+        (s = palloc((void **)&nrm, 8 * (iters + 2), st))) {
         cleanup();
         return s;
     }
@@ -891,7 +892,25 @@ bsgd_status power_iteration(const bsgd_geometry *g, int j, int iters, const int 
         row_ids = all.data();
         n_rb = g->M;
     }
+    // y-fastest copies of v and of the BP accumulator for the views whose rays
+    // run along x (optional: without them the iteration is the same, slower)
+    if (plain_wants_transpose(g, row_ids, n_rb) &&
+        (palloc((void **)&vT, n * 4, st) != BSGD_OK || palloc((void **)&wT, n * 4, st) != BSGD_OK)) {
+        pool_free(vT, st);
+        pool_free(wT, st);
+        vT = wT = nullptr;
+    }
     PlainLaunch L{row_ids, n_rb, j, j + 1, 0};
+    // A^T A v over block j: FP of v, then BP into w (and wT, added back)
+    auto ata = [&]() -> bsgd_status {
+        BSGD_CUDA(cudaMemsetAsync(y, 0, m * 4, st));
+        if (vT) BSGD_TRY(plain_transpose(g, v32, BSGD_F32, vT, j, j + 1, st));
+        BSGD_TRY(launch_fp_plain(g, L, v32, BSGD_F32, y, BSGD_F32, 1, st, vT));
+        if (wT) BSGD_CUDA(cudaMemsetAsync(wT + b0, 0, (b1 - b0) * 4, st));
+        BSGD_TRY(launch_bp_plain(g, L, y, BSGD_F32, w, 1.0f, st, wT));
+        if (wT) BSGD_TRY(plain_add_transposed(g, wT, w, j, j + 1, st));
+        return BSGD_OK;
+    };
     const int gb = grid_for(b1 - b0);
     auto run = [&]() -> bsgd_status {
         BSGD_CUDA(cudaMemsetAsync(v32, 0, n * 4, st));
@@ -899,14 +918,13 @@ bsgd_status power_iteration(const bsgd_geometry *g, int j, int iters, const int 
         BSGD_CUDA(cudaMemsetAsync(nrm, 0, 8 * (iters + 2), st));
         normalize_kernel<<<gb, 256, 0, st>>>(w, v64, v32, b0, b1, nrm, 1);
         for (int k = 0; k < iters; ++k) {
-            BSGD_CUDA(cudaMemsetAsync(y, 0, m * 4, st));
-            BSGD_TRY(launch_fp_plain(g, L, v32, BSGD_F32, y, BSGD_F32, 1, st));
-            BSGD_TRY(launch_bp_plain(g, L, y, BSGD_F32, w, 1.0f, st));
+            BSGD_TRY(ata());
             sumsq_kernel<<<gb, 256, 0, st>>>(w, b0, b1, nrm + k);
             normalize_kernel<<<gb, 256, 0, st>>>(w, v64, v32, b0, b1, nrm + k, 0);
         }
         BSGD_CUDA(cudaMemsetAsync(y, 0, m * 4, st));
-        BSGD_TRY(launch_fp_plain(g, L, v32, BSGD_F32, y, BSGD_F32, 1, st));
+        if (vT) BSGD_TRY(plain_transpose(g, v32, BSGD_F32, vT, j, j + 1, st));
+        BSGD_TRY(launch_fp_plain(g, L, v32, BSGD_F32, y, BSGD_F32, 1, st, vT));
         sumsq_kernel<<<grid_for(m), 256, 0, st>>>(y, 0, m, nrm + iters);
         BSGD_CUDA(cudaGetLastError());
         BSGD_CUDA(cudaMemcpyAsync(lambda, nrm + iters, 8, cudaMemcpyDeviceToHost, st));
