@@ -283,11 +283,21 @@ def _box_corners(geom: Geometry, N: int, j: int) -> np.ndarray:
                       blo[2] if i & 4 == 0 else bhi[2]] for i in range(8)])
 
 
+def view_cos_sin(t: float):
+    """cos and sin of view angle t; within 1e-9 rad of a multiple of pi / 2 the
+    angle is that multiple exactly (axis-aligned directions, as in the C
+    traversal)."""
+    k = round(t / (math.pi / 2))
+    if abs(t - k * (math.pi / 2)) <= 1e-9:
+        return ((1.0, 0.0), (0.0, 1.0), (-1.0, 0.0), (0.0, -1.0))[k % 4]
+    return math.cos(t), math.sin(t)
+
+
 def footprint(geom: Geometry, a: int, N: int, j: int):
     """Detector coordinates (u, v) of the 8 corners of J_j's box seen from view a:
     the shadow of a convex box is the convex hull of its corners' shadows."""
     X = _box_corners(geom, N, j)
-    c, s = math.cos(geom.angles[a]), math.sin(geom.angles[a])
+    c, s = view_cos_sin(geom.angles[a])
     xu = -s * X[:, 0] + c * X[:, 1]
     if geom.kind == "par2d":
         return xu, np.zeros_like(xu)

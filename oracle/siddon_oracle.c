@@ -49,10 +49,30 @@ typedef struct {
     double dso, dsd;
 } orc_geom;
 
+/* cos and sin of a view angle. An angle within 1e-9 rad of a multiple of
+ * pi / 2 is that multiple exactly: its directions are axis-aligned, so a ray
+ * of such a view that lies in a voxel face lies exactly in it (double cos(pi/2)
+ * is 6e-17, a tilt that would decide, for a ray in a face, which of the two
+ * voxel columns receives the whole ray). */
+static void orc_cos_sin(double t, double *c, double *s)
+{
+    const double quarter = 1.5707963267948966; /* pi / 2 */
+    const double k = nearbyint(t / quarter);
+    if (fabs(t - k * quarter) <= 1e-9) {
+        const long long m = (((long long)k % 4) + 4) % 4;
+        *c = m == 0 ? 1.0 : (m == 2 ? -1.0 : 0.0);
+        *s = m == 1 ? 1.0 : (m == 3 ? -1.0 : 0.0);
+        return;
+    }
+    *c = cos(t);
+    *s = sin(t);
+}
+
 /* End points p0, p1 of the ray of pixel (u, v) at view a. */
 static void orc_ray(const orc_geom *g, int a, int v, int u, double p0[3], double p1[3])
 {
-    double c = cos(g->angles[a]), s = sin(g->angles[a]);
+    double c, s;
+    orc_cos_sin(g->angles[a], &c, &s);
     double uc = (u - 0.5 * (g->nu - 1)) * g->du;
     double vc = (v - 0.5 * (g->nv - 1)) * g->dv;
     if (g->kind == 0) {

@@ -53,11 +53,30 @@ struct Vec3 {
     double x, y, z;
 };
 
+// cos and sin of view angle b. Within 1e-9 rad of a multiple of pi / 2 the
+// angle is that multiple exactly: the view's directions are axis-aligned, so a
+// ray that lies in a voxel face lies exactly in it, in FP32 as well (double
+// cos(pi / 2) is 6e-17, a tilt that would decide which of the face's two voxel
+// columns receives the whole ray).
+void view_cos_sin(double b, double *c, double *s) {
+    const double quarter = 1.5707963267948966;   // pi / 2
+    const double k = std::nearbyint(b / quarter);
+    if (std::fabs(b - k * quarter) <= 1e-9) {
+        const long long m = (((long long)k % 4) + 4) % 4;
+        *c = m == 0 ? 1.0 : (m == 2 ? -1.0 : 0.0);
+        *s = m == 1 ? 1.0 : (m == 3 ? -1.0 : 0.0);
+        return;
+    }
+    *c = std::cos(b);
+    *s = std::sin(b);
+}
+
 // Detector coordinates (u, v) of the shadow of point X at view angle b
 // (divergent beams): the ray from the source through X meets the detector plane
 // at t = dsd / (dso - X . e_r), u = t (X . e_u), v = t X_z.
 void shadow(const bsgd_geometry_desc &d, double b, const Vec3 &X, double *u, double *v) {
-    double c = std::cos(b), s = std::sin(b);
+    double c, s;
+    view_cos_sin(b, &c, &s);
     double xu = -s * X.x + c * X.y;
     if (d.kind == BSGD_PAR2D) {
         *u = xu;
@@ -250,7 +269,8 @@ bsgd_status build_host_tables(const bsgd_geometry_desc *desc, int M, int N, bsgd
     // Rays are addressed by the pixel's offset from the detector centre,
     // (u - (nu-1)/2, v - (nv-1)/2), which FP32 holds exactly.
     for (int a = 0; a < d.n_views; ++a) {
-        const double c = std::cos(g->angles[a]), s = std::sin(g->angles[a]);
+        double c, s;
+        view_cos_sin(g->angles[a], &c, &s);
         const double er[3] = {c, s, 0.0}, eu[3] = {-s, c, 0.0}, ev[3] = {0.0, 0.0, 1.0};
         double p0[3], pu[3], c0[3], cu[3], cv[3];
         if (d.kind == BSGD_PAR2D) {
@@ -365,8 +385,11 @@ extern "C" bsgd_status bsgd_geometry_create(const bsgd_geometry_desc *desc, int 
     // views whose rays run mostly along x (|cos| > |sin| of the view angle)
     // use the y-fastest copies of the solver state (volumes only)
     std::vector<unsigned char> yfast(d.n_views, 0);
-    for (int a = 0; a < d.n_views && d.nz > 1; ++a)
-        yfast[a] = std::fabs(std::cos(g->angles[a])) > std::fabs(std::sin(g->angles[a])) ? 1 : 0;
+    for (int a = 0; a < d.n_views && d.nz > 1; ++a) {
+        double c, s;
+        view_cos_sin(g->angles[a], &c, &s);
+        yfast[a] = std::fabs(c) > std::fabs(s) ? 1 : 0;
+    }
     g->view_yfast = yfast;
     bsgd_status st = BSGD_OK;
     int dev = 0;

@@ -17,6 +17,14 @@ SPECS = {
     "cone_small": dict(kind="cone3d", nx=40, ny=36, nz=32, dx=1.0, dy=1.0, dz=1.0, n_views=24,
                        nu=45, nv=37, du=1.6, dv=1.6, dso=120.0, dsd=240.0, M=4, N=4,
                        angles=0.05 + np.arange(24) * (2 * math.pi / 24)),
+    # degenerate cone beam: views at exact multiples of 45 deg (rays in voxel
+    # faces, x / y crossing ties), even volume sides (the central rays lie in
+    # the x = 0, y = 0 and z = 0 faces), a detector wider and taller than the
+    # volume's shadow (rays that miss), one view per row block and one slice per
+    # column block
+    "cone_axes": dict(kind="cone3d", nx=24, ny=20, nz=16, dx=1.0, dy=1.0, dz=1.0, n_views=8,
+                      nu=41, nv=33, du=1.6, dv=1.6, dso=60.0, dsd=120.0, M=8, N=16,
+                      angles=np.arange(8) * (math.pi / 4)),
     # Sec. 5, Table 1 case 1: 256^3 (1 mm), 360 views at 1 deg, 400^2 detector of
     # 1 mm, source 1536 mm / detector 1000 mm from the centre; M = 5 groups of 72
     # views (a seeded random partition, as in Sec. 5), N = 8

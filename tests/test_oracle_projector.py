@@ -143,6 +143,33 @@ def test_ray_in_a_face_belongs_to_the_voxel_above():
         expect = np.zeros((4, 4))
         expect[y + 2, :] = 1.0
         np.testing.assert_allclose(A[0, u], expect, rtol=0, atol=1e-12)
+    # view 1 (90 deg, axis-aligned exactly): rays along +y at x = 1, 0, -1 lie
+    # in faces between pixel columns
+    for u, x in enumerate((1, 0, -1)):
+        expect = np.zeros((4, 4))
+        expect[:, x + 2] = 1.0
+        np.testing.assert_allclose(A[1, u], expect, rtol=0, atol=1e-12)
+
+
+def test_axis_aligned_view_angles_are_exact():
+    """Angles within 1e-9 rad of a multiple of 90 deg give exact axis
+    directions (double cos(pi / 2) is 6e-17); other angles are untouched."""
+    for k in range(-4, 9):
+        c, s = P.view_cos_sin(k * (math.pi / 2))
+        assert (c, s) == ((1.0, 0.0), (0.0, 1.0), (-1.0, 0.0), (0.0, -1.0))[k % 4]
+    t = 2 * math.pi * 90 / 360
+    assert P.view_cos_sin(t) == (0.0, 1.0)
+    for t in (1e-6, math.pi / 2 + 1e-6, 0.3, -2.0):
+        assert P.view_cos_sin(t) == (math.cos(t), math.sin(t))
+    # the C traversal applies the same rule: a 90-deg cone view whose central
+    # column lies in the x = 0 face puts the whole ray into the + side column
+    geom = P.Geometry("cone3d", 4, 4, 2, 1.0, 1.0, 1.0, 1, 3, 3, 1.0, 1.0, dso=10.0, dsd=20.0,
+                      angles=np.array([2 * math.pi * 90 / 360]))
+    A = P.dense_matrix(geom).reshape(3, 3, 2, 4, 4)
+    col = A[1, 1]                      # centre pixel: the ray x = 0, z = 0 along -y
+    expect = np.zeros((2, 4, 4))
+    expect[1, :, 2] = 1.0              # + side in x (column 2) and in z (slice 1)
+    np.testing.assert_allclose(col, expect, rtol=0, atol=1e-12)
 
 
 def test_disc_chords_converge_first_order():
