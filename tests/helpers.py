@@ -25,6 +25,13 @@ SPECS = {
     "cone_axes": dict(kind="cone3d", nx=24, ny=20, nz=16, dx=1.0, dy=1.0, dz=1.0, n_views=8,
                       nu=41, nv=33, du=1.6, dv=1.6, dso=60.0, dsd=120.0, M=8, N=16,
                       angles=np.arange(8) * (math.pi / 4)),
+    # parallel beam whose bins all lie in pixel faces at 0 and 90 deg: unit
+    # bins at integer offsets, including the two outer faces y = +-8 (the + side
+    # convention puts the lower one inside, the upper one outside) and the
+    # boundaries between the 4-row column blocks
+    "par_faces": dict(kind="par2d", nx=16, ny=16, nz=1, dx=1.0, dy=1.0, dz=1.0, n_views=4,
+                      nu=19, nv=1, du=1.0, dv=1.0, M=2, N=4,
+                      angles=np.arange(4) * (math.pi / 4)),
     # Sec. 5, Table 1 case 1: 256^3 (1 mm), 360 views at 1 deg, 400^2 detector of
     # 1 mm, source 1536 mm / detector 1000 mm from the centre; M = 5 groups of 72
     # views (a seeded random partition, as in Sec. 5), N = 8

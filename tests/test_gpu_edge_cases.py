@@ -27,13 +27,14 @@ def _nmax(s):
     return 2 * (s["nx"] + s["ny"] + s["nz"])
 
 
-def _geoms():
-    s = spec("cone_axes")
+def _geoms(name="cone_axes"):
+    s = spec(name)
     return s, oracle_geom(s), gpu_geom(s)
 
 
-def test_axis_views_forward_and_back_projection():
-    s, og, gg = _geoms()
+@pytest.mark.parametrize("name", ["cone_axes", "par_faces"])
+def test_axis_views_forward_and_back_projection(name):
+    s, og, gg = _geoms(name)
     x = synth.uniform_array(og.n_cols, 21)
     y = torch.zeros(og.n_rows, device=DEV)
     B.bsgd_forward_project(gg, _cuda(x), y)
@@ -43,7 +44,13 @@ def test_axis_views_forward_and_back_projection():
     assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) - tol)
     # the detector overhangs the volume's shadow: some rays meet nothing
     chords = P.fp(og, np.ones(og.n_cols)).reshape(-1)
-    assert (chords == 0).sum() > 0.1 * og.n_rows
+    if name == "cone_axes":
+        assert (chords == 0).sum() > 0.1 * og.n_rows
+    else:
+        # view 0: bins 1..16 (y = -8 .. 7) each own one full pixel row, the
+        # bins at y = 8 and 9 and y = -9 miss
+        np.testing.assert_allclose(chords[:19], [0] + [16] * 16 + [0, 0], rtol=0, atol=1e-12)
+        assert np.all(np.abs(got[:19][chords[:19] == 0]) == 0)
     assert np.all(np.abs(got[chords == 0]) <= tol[chords == 0])
     r = synth.normal_array(og.n_rows, 22)
     xb = torch.zeros(og.n_cols, device=DEV)
@@ -101,15 +108,20 @@ def test_update_count_with_face_rays():
     assert abs(n_gpu - n_orc) <= 1e-5 * n_orc + 2
 
 
-def test_trajectory_with_single_view_single_slice_blocks():
-    """128 pairs of (one view, one slice), uniform draws shared with the
-    oracle by the sampling spec: two epochs give the same image."""
-    s, og, gg = _geoms()
+@pytest.mark.parametrize("name,epochs", [("cone_axes", 2), ("par_faces", 10)])
+def test_trajectory_with_single_view_single_slice_blocks(name, epochs):
+    """cone_axes: 128 pairs of (one view, one slice); par_faces: rays in
+    pixel faces and on block boundaries. Uniform draws shared with the oracle
+    by the sampling spec give the same image."""
+    s, og, gg = _geoms(name)
     M, N = s["M"], s["N"]
-    xt = synth.ellipsoid_phantom(og.nx, og.ny, og.nz, 4, seed=3).astype(np.float64).reshape(-1)
+    if og.nz > 1:
+        xt = synth.ellipsoid_phantom(og.nx, og.ny, og.nz, 4, seed=3).astype(np.float64).reshape(-1)
+    else:
+        xt = synth.ellipse_phantom(og.nx, og.ny, 4, seed=3).reshape(-1)
     y = P.fp(og, xt).reshape(-1).astype(np.float32).astype(np.float64)
     mu = 0.25 * OB.step_strip(og, N, 1.0, 30)
-    iters = 2 * M * N
+    iters = epochs * M * N
     prm = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu, seed=9)
     st = B.State(gg, prm, _cuda(y))
     x = torch.zeros(gg.n_cols, device=DEV)
