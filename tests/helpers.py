@@ -32,6 +32,10 @@ SPECS = {
     "par_faces": dict(kind="par2d", nx=16, ny=16, nz=1, dx=1.0, dy=1.0, dz=1.0, n_views=4,
                       nu=19, nv=1, du=1.0, dv=1.0, M=2, N=4,
                       angles=np.arange(4) * (math.pi / 4)),
+    # the solver's block-count limits: M = 64 row blocks (one view each) and
+    # M x N = 1024 residual-weighted pairs
+    "limits": dict(kind="cone3d", nx=16, ny=16, nz=16, dx=1.0, dy=1.0, dz=1.0, n_views=64,
+                   nu=21, nv=19, du=1.3, dv=1.3, dso=60.0, dsd=120.0, M=64, N=16),
     # Sec. 5, Table 1 case 1: 256^3 (1 mm), 360 views at 1 deg, 400^2 detector of
     # 1 mm, source 1536 mm / detector 1000 mm from the centre; M = 5 groups of 72
     # views (a seeded random partition, as in Sec. 5), N = 8

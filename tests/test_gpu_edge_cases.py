@@ -172,3 +172,45 @@ def test_calls_without_work():
     assert torch.equal(y, y0)
     B.bsgd_back_project(gg, torch.zeros(og.n_rows, device=DEV), x, accumulate=True)
     assert torch.equal(x, x0)
+
+
+def test_block_count_limits():
+    """M = 64 row blocks and M x N = 1024 pairs, the largest the device sampler
+    takes: residual-weighted draws replayed by the oracle give the same image,
+    and the oracle's own sampler agrees with the draws; then 64 pairs per
+    iteration (alpha = 1/8, gamma = 1/2, uniform) against the oracle's
+    trajectory."""
+    s, og, gg = _geoms("limits")
+    M, N = s["M"], s["N"]
+    assert M * N == 1024
+    xt = synth.ellipsoid_phantom(og.nx, og.ny, og.nz, 4, seed=5).astype(np.float64).reshape(-1)
+    y = P.fp(og, xt).reshape(-1).astype(np.float32).astype(np.float64)
+    mu = 0.25 * OB.step_strip(og, N, 1.0, 30)
+    iters = 300
+    prm = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu, seed=6,
+                        pair_sampling=B.PAIRS_RESIDUAL)
+    st = B.State(gg, prm, _cuda(y))
+    x = torch.zeros(gg.n_cols, device=DEV)
+    st.block_step(x, iters)
+    torch.cuda.synchronize()
+    tr = st.read_trace(iters)
+    po = OB.Params(M, N, 1 / M, 1 / N, mu, seed=6, pair_sampling="residual")
+    ost = OB.BSGDState(og, y, po)
+    agree = 0
+    for t in tr:
+        assert int(t[0]) == 1
+        sel = OB.Selection([(int(t[1]), int(t[2]))], [None])
+        agree += OB.sample(og, po, ost.it, ost.r, ost.bands, ost.cell_w).pairs == sel.pairs
+        ost.step(sel)
+    assert rel_l2(x.cpu().double().numpy(), ost.x) <= 1e-5
+    assert agree >= iters - 2
+    # 8 x 8 = 64 pairs per iteration (the work list's capacity)
+    kM, kN, iters = 8, 8, 12
+    prm = B.SolveParams(alpha=kM / M, gamma=kN / N, step_rule=B.STEP_FIXED, mu=mu, seed=7)
+    st = B.State(gg, prm, _cuda(y))
+    x = torch.zeros(gg.n_cols, device=DEV)
+    st.block_step(x, iters)
+    torch.cuda.synchronize()
+    assert np.all(st.read_trace(iters)[:, 0] == kM * kN)
+    ost = OB.bsgd(og, y, OB.Params(M, N, kM / M, kN / N, mu, seed=7), iters)
+    assert rel_l2(x.cpu().double().numpy(), ost.x) <= 1e-5
