@@ -379,20 +379,35 @@ __device__ void update_body(const DeviceGeom &G, const SolveDev &S, T *__restric
         const int64_t bT = plane + (int64_t)x0 * ny + y0;   // + k * ny + lane
         const int64_t bX = plane + (int64_t)y0 * nx + x0;   // + k * nx + lane
         const bool full = x0 + 32 <= nx && y0 + 32 <= ny;
-        __syncthreads();
+        // every global load of the tile first (the gT rows to transpose, this
+        // thread's g and x values): one round of memory latency per tile
+        float gt[4], gv[4], xs[4];
 #pragma unroll
-        for (int k = row; k < 32; k += 8) {           // gT rows: fixed x, consecutive y
-            const bool in = full || (x0 + k < nx && y0 + lane < ny);
-            sg[k][lane] = in ? S.gT[bT + k * ny + lane] : 0.f;
+        for (int q = 0; q < 4; ++q) {
+            const int k = row + 8 * q;
+            const bool inT = full || (x0 + k < nx && y0 + lane < ny);   // gT rows: fixed x
+            gt[q] = inT ? S.gT[bT + k * ny + lane] : 0.f;
+            const bool inX = full || (y0 + k < ny && x0 + lane < nx);   // x rows: fixed y
+            const int64_t idx = bX + k * nx + lane;
+            gv[q] = inX ? S.g[idx] : 0.f;
+            xs[q] = inX ? (xlo ? ldv(x + idx) + ldv(xlo + idx) : ldv(x + idx)) : 0.f;
         }
+        __syncthreads();   // the previous tile's xT stores are done with sx
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sg[row + 8 * q][lane] = gt[q];
         __syncthreads();
 #pragma unroll
-        for (int k = row; k < 32; k += 8) {           // x rows: fixed y, consecutive x
+        for (int q = 0; q < 4; ++q) {
+            const int k = row + 8 * q;
             if (full || (y0 + k < ny && x0 + lane < nx)) {
                 const int64_t idx = bX + k * nx + lane;
-                const float gv = S.g[idx] + sg[lane][k];
-                sx[k][lane] = updated(x, xlo, idx, mu, gv, x, xlo);
-                if (S.eud) S.eud[idx] += gv;
+                const float g = gv[q] + sg[lane][k];
+                const float s = fmaf(mu, g, xs[q]);
+                const float hi = rnd(s, x);
+                stf(x + idx, hi);
+                if (xlo) stf(xlo + idx, s - hi);
+                sx[k][lane] = hi;
+                if (S.eud) S.eud[idx] += g;
             }
         }
         __syncthreads();
@@ -403,17 +418,18 @@ __device__ void update_body(const DeviceGeom &G, const SolveDev &S, T *__restric
     }
 }
 
-// The block update of this iteration (every CTA but the last row) and the
-// draw of the next iteration (the first CTA of the last row).
+// The block update of this iteration (CTAs x >= 1 of each row) and the draw
+// of the next iteration (CTA (0, 0), the first one dispatched, so that the
+// one-CTA draw runs beside the update instead of after it).
 template <typename T>
 __global__ void __launch_bounds__(256) update_sample_kernel(const DeviceGeom G, const SolveDev S,
                                                             T *__restrict__ x, T *__restrict__ xlo,
                                                             const SampleArgs An) {
-    if (blockIdx.y == gridDim.y - 1) {
-        if (blockIdx.x == 0) sample_body(An);
+    if (blockIdx.x == 0) {
+        if (blockIdx.y == 0) sample_body(An);
         return;
     }
-    update_body<T>(G, S, x, xlo, blockIdx.y, blockIdx.x, gridDim.x);
+    update_body<T>(G, S, x, xlo, blockIdx.y, blockIdx.x - 1, gridDim.x - 1);
 }
 
 // xT = transpose(x) over the whole volume (y fastest), through shared memory.
@@ -1383,7 +1399,7 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st, bool d
         // once this iteration's FPs are done: one extra CTA of the update
         SampleArgs An;
         fill_sample_args(s, An, k + 1);
-        dim3 ugs(ug.x, ug.y + 1);
+        dim3 ugs(ug.x + 1, ug.y);
         if (s->st == BSGD_F32)
             update_sample_kernel<float><<<ugs, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr, An);
         else if (s->st == BSGD_BF16)
