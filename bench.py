@@ -48,7 +48,7 @@ ALU_OPS_PER_UPDATE = 5
 # launches of one epoch of this workload, from one ncu capture of the current
 # kernel (profiles/fpbp_solve_kernel_cone256_dram_traffic.md); null for the
 # split kernels, which were not captured.
-TRAFFIC_PER_LAUNCH = {"fpbp": 46_502_516}
+TRAFFIC_PER_LAUNCH = {"fpbp": 46_481_784}
 
 
 # Serving workload: Poisson arrivals (20 / s), request sizes n^3 with (256 / n) mm

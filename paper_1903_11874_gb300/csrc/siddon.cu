@@ -2,10 +2,12 @@
 // and the two solver kernels of one BSGD iteration (FP with the fused residual
 // update, BP of the residual change).
 //
-// Grid: x = tile of the detector band (128 rays per CTA), y = view slot inside
-// the selected row block(s), z = pair slot (solver). A CTA's rays all belong to
-// one view and one column block, so they share the view's ray table entry and
-// walk a compact bundle of neighbouring voxels.
+// Grid of the plain kernels and the solver's BP: x = tile of the detector band
+// (128 rays per CTA), y = view slot inside the selected row block(s), z = pair
+// slot (solver). Solver FP and fused kernels: x = tile x view slots with the
+// view slot fastest, z = pair slot. A CTA's rays all belong to one view and one
+// column block, so they share the view's ray table entry and walk a compact
+// bundle of neighbouring voxels.
 #include <algorithm>
 
 #include "siddon_device.cuh"
@@ -327,13 +329,13 @@ __device__ __forceinline__ void fpbp_solve_body(const DeviceGeom &G, const Solve
 template <typename T>
 __global__ void __launch_bounds__(128) fpbp_solve_kernel(const DeviceGeom G, const SolveDev S,
                                                          const T *__restrict__ x) {
-    fpbp_solve_body<T>(G, S, x, blockIdx.x, blockIdx.y, blockIdx.z);
+    fpbp_solve_body<T>(G, S, x, blockIdx.x / G.max_views, blockIdx.x % G.max_views, blockIdx.z);
 }
 
 template <typename T, bool FUSED>
 __global__ void __launch_bounds__(128) fp_solve_kernel(const DeviceGeom G, const SolveDev S,
                                                        const T *__restrict__ x) {
-    fp_solve_body<T, FUSED>(G, S, x, blockIdx.x, blockIdx.y, blockIdx.z);
+    fp_solve_body<T, FUSED>(G, S, x, blockIdx.x / G.max_views, blockIdx.x % G.max_views, blockIdx.z);
 }
 
 template <typename T>
@@ -365,10 +367,10 @@ __global__ void __launch_bounds__(128) round_solve_kernel(const ReqDesc *__restr
         const ReqDesc &q = T[round_entry(T, C->n, item)];
         if (!q.active || item >= q.work_begin + q.work_count) continue;
         long long local = item - q.work_begin;
-        const int tile = (int)(local % q.max_tiles);
-        local /= q.max_tiles;
         const int slot = (int)(local % q.G.max_views);
-        const int p = (int)(local / q.G.max_views);
+        local /= q.G.max_views;
+        const int tile = (int)(local % q.max_tiles);
+        const int p = (int)(local / q.max_tiles);
         if (q.dtype == BSGD_F32)
             fpbp_solve_body<float>(q.G, q.S, (const float *)q.x, tile, slot, p);
         else if (q.dtype == BSGD_BF16)
@@ -570,7 +572,9 @@ bsgd_status launch_count_cells(const bsgd_geometry *g, int j, int n_cells,
 bsgd_status launch_fp_solve(const bsgd_geometry *g, const SolveDev &S, const void *x,
                             bsgd_dtype st_t, int max_pairs, int max_tiles, bool fused,
                             cudaStream_t st) {
-    dim3 grid(max_tiles, g->max_views, max_pairs);
+    // view slot fastest: CTAs running together hold the same band rows of
+    // every view, and a launch ends on the band's last (edge) rows
+    dim3 grid((unsigned)max_tiles * g->max_views, 1, max_pairs);
 #define FPS_GO(T)                                                                          \
     if (fused) fp_solve_kernel<T, true><<<grid, 128, 0, st>>>(g->dg, S, (const T *)x);     \
     else fp_solve_kernel<T, false><<<grid, 128, 0, st>>>(g->dg, S, (const T *)x);
@@ -584,7 +588,9 @@ bsgd_status launch_fp_solve(const bsgd_geometry *g, const SolveDev &S, const voi
 
 bsgd_status launch_fpbp_solve(const bsgd_geometry *g, const SolveDev &S, const void *x,
                               bsgd_dtype st_t, int max_pairs, int max_tiles, cudaStream_t st) {
-    dim3 grid(max_tiles, g->max_views, max_pairs);
+    // view slot fastest: CTAs running together hold the same band rows of
+    // every view, and a launch ends on the band's last (edge) rows
+    dim3 grid((unsigned)max_tiles * g->max_views, 1, max_pairs);
     if (st_t == BSGD_F32) fpbp_solve_kernel<float><<<grid, 128, 0, st>>>(g->dg, S, (const float *)x);
     else if (st_t == BSGD_BF16) fpbp_solve_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(g->dg, S, (const __nv_bfloat16 *)x);
     else fpbp_solve_kernel<__half><<<grid, 128, 0, st>>>(g->dg, S, (const __half *)x);
@@ -594,6 +600,9 @@ bsgd_status launch_fpbp_solve(const bsgd_geometry *g, const SolveDev &S, const v
 
 bsgd_status launch_bp_solve(const bsgd_geometry *g, const SolveDev &S, bsgd_dtype st_t,
                             int max_pairs, int max_tiles, cudaStream_t st) {
+    // tile fastest: the BP alone scatters faster when the CTAs running
+    // together hold different views (their atomics spread over more of g);
+    // the FP and the fused kernel gather faster with the view slot fastest
     dim3 grid(max_tiles, g->max_views, max_pairs);
     if (st_t == BSGD_F32) bp_solve_kernel<float><<<grid, 128, 0, st>>>(g->dg, S);
     else if (st_t == BSGD_BF16) bp_solve_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(g->dg, S);
