@@ -568,14 +568,29 @@ def paper_scale_leg(B, torch, dev, cases, warm=2, iters=10):
         prof = st.read_profile()
         q1 = st.query()
         upd = (q1["updates"] - q0["updates"]) / iters
+        # the same iterations with FP, residual and BP as separate passes: the
+        # per-iteration FP and BP times of Sec. 5's comparison
+        st.set_split(True)
+        st.profile(False)
+        st.block_step(x, 1)
+        torch.cuda.synchronize()
+        st.profile(True)
+        ev0.record()
+        st.block_step(x, iters)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms_split = ev0.elapsed_time(ev1) / iters
+        prs = st.read_profile()
         out[name] = {
             "volume": "%d^3 (%.2f mm)" % (n, 256.0 / n), "detector": "%d^2 (%.2f mm)" % (nd, 400.0 / nd),
             "rows": gg.n_rows, "cols": gg.n_cols, "blocks": "M=5 (random partition), N=8 z-slabs, "
             "alpha=1/5, gamma=2/8",
             "ms_per_iteration": round(ms, 3),
-            "fp_ms_per_iteration": round(prof["fp"]["ms"] / iters, 3),
-            "residual_ms_per_iteration": round(prof["residual"]["ms"] / iters, 3),
-            "bp_ms_per_iteration": round(prof["bp"]["ms"] / iters, 3),
+            "fused_ms_per_iteration": round(prof["fpbp"]["ms"] / iters, 3),
+            "split_ms_per_iteration": round(ms_split, 3),
+            "fp_ms_per_iteration": round(prs["fp"]["ms"] / iters, 3),
+            "residual_ms_per_iteration": round(prs["residual"]["ms"] / iters, 3),
+            "bp_ms_per_iteration": round(prs["bp"]["ms"] / iters, 3),
             "updates_per_iteration": int(upd),
             "value": round(upd / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
             "state_setup_s": round(t_setup, 2), "step": "strip, 5 power iterations" if n <= 512

@@ -332,6 +332,117 @@ __global__ void __launch_bounds__(128) fpbp_solve_kernel(const DeviceGeom G, con
     fpbp_solve_body<T>(G, S, x, blockIdx.x / G.max_views, blockIdx.x % G.max_views, blockIdx.z);
 }
 
+// FP, residual and BP of one ray in one pass when an iteration selects several
+// column blocks (at most NC) and no detector cells: the ray's new residual
+// needs the new z^j of every selected block, so the thread walks each selected
+// slab forward, forms r = y - sum_j z^j, then walks each slab back with that
+// block's own snapshot difference r - r~^j. The work item is a tile of the
+// bounding box of the selected blocks' bands (the rows the split path's
+// residual pass covers) for one view of one selected row block (rs).
+template <typename T, int NC>
+__device__ __forceinline__ void fpbpm_solve_body(const DeviceGeom &G, const SolveDev &S,
+                                                 const T *__restrict__ x, int tile, int slot,
+                                                 int rs) {
+    const Work &W = *S.work;
+    if (rs >= W.n_rows) return;
+    const int i = W.rows[rs];
+    if (slot >= G.block_nviews[i]) return;
+    const int a = G.block_views[i * G.max_views + slot];
+    int js[NC];
+    Band b{1 << 30, -1, 1 << 30, -1};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        js[c] = c < W.n_cols ? W.cols[c] : -1;
+        if (js[c] < 0) continue;
+        const Band q = G.bands[(size_t)a * (G.N + 1) + js[c]];
+        if (q.u0 > q.u1 || q.v0 > q.v1) continue;
+        b.u0 = min(b.u0, q.u0);
+        b.u1 = max(b.u1, q.u1);
+        b.v0 = min(b.v0, q.v0);
+        b.v1 = max(b.v1, q.v1);
+    }
+    int u, v, nt;
+    const bool act = G.nv > 1 ? tile_pixel<true>(b, tile, u, v, nt) : tile_pixel<false>(b, tile, u, v, nt);
+    if (tile >= nt) return;   // uniform over the CTA
+    const bool yf = S.xT != nullptr && G.view_yfast[a];
+    const T *src = yf ? reinterpret_cast<const T *>(S.xT) : x;
+    T *z = reinterpret_cast<T *>(S.z);
+    float zn[NC];
+    int64_t kj[NC];
+    bool in[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        zn[c] = 0.f;
+        in[c] = false;
+        kj[c] = 0;
+        if (!act || js[c] < 0) continue;
+        kj[c] = zslot(G, js[c], a, u, v, in[c]);
+        if (!in[c]) continue;   // z^j is 0 outside block j's band
+        RayWalk w;
+        if (ray_setup(G, a, u, v, G.plane_start[js[c]], G.plane_start[js[c] + 1], w, yf)) {
+            float acc = 0.f;
+            ray_walk_fast(w, [&](int idx, float s) { acc = fmaf(s, ldf(src + idx), acc); });
+            zn[c] = acc * w.L;
+        }
+        stf(z + kj[c], zn[c]);
+        zn[c] = rnd(zn[c], z);
+    }
+    const int64_t row = act ? ((int64_t)a * G.nv + v) * G.nu + u : 0;
+    T *r = reinterpret_cast<T *>(S.r);
+    double dn = 0.0;
+    float rn = 0.f;
+    if (act) {
+        float zs = 0.f;
+        for (int jj = 0; jj < G.N; ++jj) {   // z^jj is 0 outside block jj's band
+            bool sel = false;
+            float zv = 0.f;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (jj == js[c]) {
+                    sel = true;
+                    zv = zn[c];
+                }
+            if (sel) {
+                zs += zv;
+                continue;
+            }
+            bool inj;
+            const int64_t k = zslot(G, jj, a, u, v, inj);
+            if (inj) zs += ldv(z + k);
+        }
+        rn = rnd(ldf(reinterpret_cast<const T *>(S.y) + row) - zs, r);
+        const float ro = ldv(r + row);
+        stf(r + row, rn);
+        dn = (double)rn * rn - (double)ro * ro;
+    }
+    // the 32 lanes of a warp share one detector row; lane 0 has the lowest u,
+    // so it is active whenever any lane of the warp is
+    for (int o = 16; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+    if ((threadIdx.x & 31) == 0 && act && dn != 0.0) atomicAdd(S.S + (size_t)i * G.nv + v, dn);
+    const bool yb = S.gT != nullptr && G.view_yfast[a];
+    float *dst = yb ? S.gT : S.g;
+    T *rt = reinterpret_cast<T *>(S.rt);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        if (!act || !in[c]) continue;
+        const float dw = rn - ldv(rt + kj[c]);
+        stf(rt + kj[c], rn);
+        if (dw == 0.f) continue;
+        RayWalk w;
+        if (!ray_setup(G, a, u, v, G.plane_start[js[c]], G.plane_start[js[c] + 1], w, yb)) continue;
+        const float wl = dw * w.L;
+        ray_walk_fast(w, [&](int idx, float s) {
+            if (s > 0.f) atomicAdd(dst + idx, s * wl);
+        });
+    }
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(128) fpbpm_solve_kernel(const DeviceGeom G, const SolveDev S,
+                                                          const T *__restrict__ x) {
+    fpbpm_solve_body<T, NC>(G, S, x, blockIdx.x / G.max_views, blockIdx.x % G.max_views, blockIdx.z);
+}
+
 template <typename T, bool FUSED>
 __global__ void __launch_bounds__(128) fp_solve_kernel(const DeviceGeom G, const SolveDev S,
                                                        const T *__restrict__ x) {
@@ -594,6 +705,24 @@ bsgd_status launch_fpbp_solve(const bsgd_geometry *g, const SolveDev &S, const v
     if (st_t == BSGD_F32) fpbp_solve_kernel<float><<<grid, 128, 0, st>>>(g->dg, S, (const float *)x);
     else if (st_t == BSGD_BF16) fpbp_solve_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(g->dg, S, (const __nv_bfloat16 *)x);
     else fpbp_solve_kernel<__half><<<grid, 128, 0, st>>>(g->dg, S, (const __half *)x);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+bsgd_status launch_fpbpm_solve(const bsgd_geometry *g, const SolveDev &S, const void *x,
+                               bsgd_dtype st_t, int max_rows, int max_tiles, int n_cols,
+                               cudaStream_t st) {
+    if (n_cols < 2 || n_cols > kMaxFusedCols)
+        return fail(BSGD_ERR_INVALID_ARG, "fused multi-block pass takes 2 to 4 column blocks");
+    // view slot fastest, as in the one-block fused kernel
+    dim3 grid((unsigned)max_tiles * g->max_views, 1, max_rows);
+#define FPBPM_GO(T, NC) fpbpm_solve_kernel<T, NC><<<grid, 128, 0, st>>>(g->dg, S, (const T *)x);
+#define FPBPM_T(T) if (n_cols <= 2) { FPBPM_GO(T, 2) } else { FPBPM_GO(T, 4) }
+    if (st_t == BSGD_F32) { FPBPM_T(float) }
+    else if (st_t == BSGD_BF16) { FPBPM_T(__nv_bfloat16) }
+    else { FPBPM_T(__half) }
+#undef FPBPM_T
+#undef FPBPM_GO
     BSGD_CUDA(cudaGetLastError());
     return BSGD_OK;
 }

@@ -706,6 +706,7 @@ struct bsgd_state {
     bsgd_dtype st = BSGD_F32;
     bool fused = true;
     int max_tiles = 0;
+    int max_tiles_all = 0;      // tiles of the whole-volume band (bounds any union of bands)
     int n_cells = 1;
     int stride = 0;
     int64_t trace_cap = 0;
@@ -1182,6 +1183,7 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     for (int a = 0; a < V; ++a) all[a] = a;
     for (int j = 0; j < N; ++j)
         s->max_tiles = std::max(s->max_tiles, tiles_for(g, all, j, j + 1, tile_u(g), tile_v(g)));
+    s->max_tiles_all = tiles_for(g, all, 0, N, tile_u(g), tile_v(g));
     SolveDev &d = s->dev;
     d.y = s->y;
     d.z = s->z;
@@ -1364,10 +1366,20 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st, bool d
         BSGD_CUDA(cudaGetLastError());
         stage_end(s, BSGD_STAGE_SAMPLE, b, 1, st);
     }
+    // several column blocks fuse too when every drawn row block is paired with
+    // every drawn column block (uniform draws, not a replayed trace) and no
+    // detector cells restrict the rays of a pair
+    const bool replaying = s->replay && k >= s->replay_start && k < s->replay_start + s->replay_n;
+    const bool fuse_multi = !s->fused && s->kN <= kMaxFusedCols && s->n_cells == 1 &&
+                            s->p.pair_sampling == BSGD_PAIRS_UNIFORM && !replaying;
     if (s->max_tiles > 0 && s->fused && !s->split) {
         // one column block per iteration: FP, residual and BP in one pass
         b = stage_begin(s, st);
         BSGD_TRY(launch_fpbp_solve(g, s->dev, x, s->st, s->P, s->max_tiles, st));
+        stage_end(s, BSGD_STAGE_FPBP, b, 1, st);
+    } else if (s->max_tiles > 0 && fuse_multi && !s->split) {
+        b = stage_begin(s, st);
+        BSGD_TRY(launch_fpbpm_solve(g, s->dev, x, s->st, s->kM, s->max_tiles_all, s->kN, st));
         stage_end(s, BSGD_STAGE_FPBP, b, 1, st);
     } else if (s->max_tiles > 0) {
         b = stage_begin(s, st);

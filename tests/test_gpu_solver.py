@@ -128,13 +128,45 @@ def test_fused_and_split_kernels_agree(name):
 
 def test_several_column_blocks_per_iteration():
     """alpha = gamma = 1/2 on the paper's 2D set-up: two column blocks share a
-    row block, so r is recomputed after both FPs (the unfused path)."""
+    row block, so r is formed after both blocks' FPs (the multi-block fused
+    pass), against the literal form of Algorithm 1."""
     s, og, gg, y, mu, _ = problem("paper2d")
     M, N = s["M"], s["N"]
     prm = B.SolveParams(alpha=0.5, gamma=1.0, step_rule=B.STEP_FIXED, mu=mu, seed=5)
     _, x = gpu_run(gg, y, prm, 60)
     x_lit, _ = OB.bsgd_literal(og, y, OB.Params(M, N, 0.5, 1.0, mu, seed=5), 60)
     assert rel_l2(x.cpu().double().numpy(), x_lit) <= 1e-5
+
+
+@pytest.mark.parametrize("kM,kN", [(1, 2), (2, 2), (1, 3), (1, 4), (2, 4)])
+def test_several_column_blocks_fused_pass(kM, kN):
+    """kN column blocks per iteration (uniform draws, no cells) run FP,
+    residual and BP in one pass over the bounding box of the drawn blocks'
+    bands: the same trajectory as the FP64 oracle, and as the split path
+    (FP pass, residual pass, BP pass) up to the order of the float atomics."""
+    s, og, gg, y, mu, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    iters = 3 * (M // kM) * (N // kN)
+    out = []
+    for split in (False, True):
+        prm = B.SolveParams(alpha=kM / M, gamma=kN / N, step_rule=B.STEP_FIXED, mu=mu, seed=8)
+        st = B.State(gg, prm, torch.from_numpy(y.astype(np.float32)).to(DEV))
+        st.set_split(split)
+        x = torch.zeros(gg.n_cols, device=DEV)
+        st.profile(True)
+        st.block_step(x, iters)
+        prof = st.read_profile()
+        out.append((x.cpu().double().numpy(), st.read_trace(iters), st.query(), prof))
+    (xf, tf, qf, pf), (xs, ts, qs, ps) = out
+    assert pf["fpbp"]["launches"] == iters and pf["fp"]["launches"] == 0 and pf["residual"]["launches"] == 0
+    assert ps["fp"]["launches"] == iters and ps["fpbp"]["launches"] == 0
+    assert np.array_equal(tf, ts) and np.all(tf[:, 0] == kM * kN)
+    assert rel_l2(xf, xs) <= 1e-6
+    assert qf["updates"] == qs["updates"]
+    assert abs(qf["residual_norm"] - qs["residual_norm"]) <= 1e-6 * np.linalg.norm(y)
+    ost = OB.bsgd(og, y, OB.Params(M, N, kM / M, kN / N, mu, seed=8), iters)
+    assert rel_l2(xf, ost.x) <= 1e-5
+    assert abs(qf["residual_norm"] - ost.residual_norm()) <= 1e-4 * np.linalg.norm(y)
 
 
 @pytest.mark.parametrize("pairs,cells", [(B.PAIRS_UNIFORM, B.CELLS_GEOMETRIC),
