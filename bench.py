@@ -49,6 +49,10 @@ ALU_OPS_PER_UPDATE = 5
 # kernel (profiles/fpbp_solve_kernel_cone256_dram_traffic.md); null for the
 # split kernels, which were not captured.
 TRAFFIC_PER_LAUNCH = {"fpbp": 46_481_784}
+# What does bind the fused kernel, from the same kernel's ncu --set full capture
+# (profiles/fpbp_solve_kernel_cone256_ncu_full.md, the heavier of two pairs):
+# L2 and L1/TEX throughput in % of their peaks, issue-active cycles in %.
+ON_CHIP_NCU = {"fpbp": {"l2_pct": 64.3, "l1tex_pct": 68.6, "issue_active_pct": 47.2}}
 
 
 # Serving workload: Poisson arrivals (20 / s), request sizes n^3 with (256 / n) mm
@@ -280,6 +284,7 @@ def run_cuda(args):
         "launch_ms": round(launch_ms, 4), "updates_per_launch": int(upd_per_launch),
         "hbm_algorithmic_gbs": round(hbm_ach, 1), "hbm_peak_gbs": hbm_peak,
         "hbm_frac": round(hbm_ach / hbm_peak, 4),
+        "on_chip_ncu": ON_CHIP_NCU.get(dom),
     }
     stages = {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in prof.items()
               if v["launches"]}

@@ -250,6 +250,31 @@ def test_reduced_precision_storage(storage):
     assert rel_l2(x.float().cpu().double().numpy(), ost.x) <= 1e-2
 
 
+@pytest.mark.parametrize("storage", [B.BF16, B.F16])
+def test_reduced_precision_several_column_blocks(storage):
+    """16-bit storage through the multi-block fused pass (alpha = 1/4, gamma =
+    2/4 on the small cone beam): the fused and the split path round z, r and
+    r~ at the same points, so they agree to the order of the float atomics,
+    and both stay within 1e-2 of the FP64 oracle."""
+    s, og, gg, y, mu, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    iters = 3 * 8
+    tdt = torch.bfloat16 if storage == B.BF16 else torch.float16
+    xs = []
+    for split in (False, True):
+        prm = B.SolveParams(alpha=1 / M, gamma=2 / N, step_rule=B.STEP_FIXED, mu=mu, seed=2,
+                            storage=storage)
+        st = B.State(gg, prm, torch.from_numpy(y.astype(np.float32)).to(DEV))
+        st.set_split(split)
+        x = torch.zeros(gg.n_cols, device=DEV, dtype=tdt)
+        st.block_step(x, iters)
+        torch.cuda.synchronize()
+        xs.append(x.float().cpu().double().numpy())
+    ost = OB.bsgd(og, y, OB.Params(M, N, 1 / M, 2 / N, mu, seed=2), iters)
+    assert rel_l2(xs[0], xs[1]) <= 1e-3
+    assert rel_l2(xs[0], ost.x) <= 1e-2
+
+
 def test_solve_with_host_buffers_equals_block_steps():
     s, og, gg, y, mu, _ = problem("config1")
     prm = B.SolveParams(alpha=0.25, gamma=0.25, epochs=3, step_rule=B.STEP_FIXED, mu=mu, seed=4)
