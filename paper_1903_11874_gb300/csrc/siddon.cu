@@ -2,10 +2,10 @@
 // and the two solver kernels of one BSGD iteration (FP with the fused residual
 // update, BP of the residual change).
 //
-// Grid of the plain kernels and the solver's BP: x = tile of the detector band
-// (128 rays per CTA), y = view slot inside the selected row block(s), z = pair
-// slot (solver). Solver FP and fused kernels: x = tile x view slots with the
-// view slot fastest, z = pair slot. A CTA's rays all belong to one view and one
+// Grid of the plain BP and count kernels and the solver's BP: x = tile of the
+// detector band (128 rays per CTA), y = view slot inside the selected row
+// block(s), z = pair slot (solver). FP and fused kernels: x = tile x view slots
+// with the view slot fastest (z = pair slot in the solver). A CTA's rays all belong to one view and one
 // column block, so they share the view's ray table entry and walk a compact
 // bundle of neighbouring voxels.
 #include <algorithm>
@@ -38,11 +38,13 @@ __global__ void __launch_bounds__(128) fp_plain_kernel(const DeviceGeom G, const
                                                        int j1, const TX *__restrict__ x,
                                                        TY *__restrict__ y,
                                                        const TX *__restrict__ xT) {
-    const int a = sel_view(G, R, blockIdx.y);
+    // view slot fastest (as in the solver's FP): the CTAs running together
+    // gather the same band rows of every view
+    const int a = sel_view(G, R, blockIdx.x % (R.n * G.max_views));
     if (a < 0) return;
     const Band b = band_of(G, a, j0, j1);
     int u, v, nt;
-    if (!tile_pixel<k3D>(b, blockIdx.x, u, v, nt)) return;
+    if (!tile_pixel<k3D>(b, blockIdx.x / (R.n * G.max_views), u, v, nt)) return;
     const bool yf = xT != nullptr && G.view_yfast[a];
     const TX *src = yf ? xT : x;
     RayWalk w;
@@ -624,7 +626,9 @@ bsgd_status launch_fp_plain(const bsgd_geometry *g, const PlainLaunch &L, const 
     return for_row_chunks(g, L, [&](const RowSel &R) -> bsgd_status {
         const int tiles = tiles_for(g, views_of(g, R), L.j0, L.j1, tile_u(g), tile_v(g));
         if (tiles == 0) return BSGD_OK;
-        dim3 grid(tiles, R.n * g->max_views);
+        const int64_t ctas = (int64_t)tiles * R.n * g->max_views;
+        if (ctas > 0x7fffffff) return fail(BSGD_ERR_INVALID_ARG, "forward projection grid too large");
+        dim3 grid((unsigned)ctas);
         if (xt == BSGD_F32) fp_plain_y<float>(g, grid, R, L.j0, L.j1, x, y, yt, xT, st);
         else if (xt == BSGD_BF16) fp_plain_y<__nv_bfloat16>(g, grid, R, L.j0, L.j1, x, y, yt, xT, st);
         else fp_plain_y<__half>(g, grid, R, L.j0, L.j1, x, y, yt, xT, st);

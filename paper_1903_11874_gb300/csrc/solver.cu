@@ -1184,6 +1184,10 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     for (int j = 0; j < N; ++j)
         s->max_tiles = std::max(s->max_tiles, tiles_for(g, all, j, j + 1, tile_u(g), tile_v(g)));
     s->max_tiles_all = tiles_for(g, all, 0, N, tile_u(g), tile_v(g));
+    if ((int64_t)s->max_tiles_all * g->max_views > 0x7fffffff) {
+        free_state(s);
+        return fail(BSGD_ERR_INVALID_ARG, "detector tiles x views per block exceed one launch grid");
+    }
     SolveDev &d = s->dev;
     d.y = s->y;
     d.z = s->z;
