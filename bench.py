@@ -71,6 +71,14 @@ SERVE_SMALL = dict(n_req=16, sizes=(64, 128, 256), views=(90, 180, 360), epochs=
 # gamma = 2/8 (two column blocks per iteration). Noise-free projections, as in
 # the paper's FP / BP timing runs.
 PAPER_CASES = {"case1": (256, 400), "case2": (512, 1000), "case3": (1024, 2000)}
+# Sec. 6's BSGD-IM set-up: a 256^3 grid of 1 mm voxels, 360 views, a 512^2
+# detector of 1 mm pixels, source 1000 mm and detector 536 mm from the centre;
+# M = 5, N = 8, alpha = 0.2, gamma = 0.5 (four column blocks per iteration),
+# one of four detector quadrants per view and pair drawn by Algorithm 2. The
+# paper's projections carry white noise (28.1 dB); the timing does not depend
+# on the data, so they are noise-free here.
+IM_GEOM = dict(kind="cone3d", nx=256, ny=256, nz=256, dx=1.0, dy=1.0, dz=1.0, n_views=360,
+               nu=512, nv=512, du=1.0, dv=1.0, dso=1000.0, dsd=1536.0)
 
 
 def paper_geom(n, nd):
@@ -97,8 +105,8 @@ def parse():
     ap.add_argument("--serving", default="small", choices=["off", "small", "full"])
     ap.add_argument("--split", action="store_true",
                     help="run FP and BP as two kernels (to time them apart)")
-    ap.add_argument("--paper-scale", default="case1,case2,case3",
-                    help="paper-scale cases to time (comma list of case1, case2, case3; 'off')")
+    ap.add_argument("--paper-scale", default="case1,case2,case3,im",
+                    help="paper-scale cases to time (comma list of case1, case2, case3, im; 'off')")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the BF16-storage, TV-prox and autograd legs")
     return ap.parse_args()
@@ -539,8 +547,9 @@ def paper_scale_leg(B, torch, dev, cases, warm=2, iters=10):
     from paper_1903_11874_gb300 import synth
     out = {}
     for name in cases:
-        n, nd = PAPER_CASES[name]
-        geo = paper_geom(n, nd)
+        im = name == "im"
+        n, nd = (256, 512) if im else PAPER_CASES[name]
+        geo = dict(IM_GEOM) if im else paper_geom(n, nd)
         gg = B.Geometry(M=5, N=8, view_block=paper_partition(), **geo)
         base = synth.ellipsoid_phantom(256, 256, 256, 10, seed=0) * KAPPA
         vol = torch.from_numpy(base).to(dev)
@@ -550,7 +559,11 @@ def paper_scale_leg(B, torch, dev, cases, warm=2, iters=10):
         y = torch.zeros(gg.n_rows, device=dev)
         B.bsgd_forward_project(gg, vol.reshape(-1).contiguous(), y)
         del vol
-        if n <= 512:
+        if im:
+            prm = B.SolveParams(alpha=0.2, gamma=0.5, step_rule=B.STEP_STRIP, rho=RHO,
+                                power_iters=5, pair_sampling=B.PAIRS_UNIFORM,
+                                cells=B.CELLS_GEOMETRIC, n_cells=4, seed=1)
+        elif n <= 512:
             prm = B.SolveParams(alpha=1 / 5, gamma=2 / 8, step_rule=B.STEP_STRIP, rho=RHO,
                                 power_iters=5, pair_sampling=B.PAIRS_UNIFORM, seed=1)
         else:   # a power iteration at 1024^3 takes minutes; the timing does not depend on mu
@@ -587,9 +600,12 @@ def paper_scale_leg(B, torch, dev, cases, warm=2, iters=10):
         ms_split = ev0.elapsed_time(ev1) / iters
         prs = st.read_profile()
         out[name] = {
-            "volume": "%d^3 (%.2f mm)" % (n, 256.0 / n), "detector": "%d^2 (%.2f mm)" % (nd, 400.0 / nd),
-            "rows": gg.n_rows, "cols": gg.n_cols, "blocks": "M=5 (random partition), N=8 z-slabs, "
-            "alpha=1/5, gamma=2/8",
+            "volume": "%d^3 (%.2f mm)" % (n, 256.0 / n),
+            "detector": "%d^2 (%.2f mm)" % (nd, geo["du"]),
+            "rows": gg.n_rows, "cols": gg.n_cols,
+            "blocks": "M=5 (random partition), N=8 z-slabs, " + (
+                "alpha=0.2, gamma=0.5, geometric detector quadrants (Algorithm 2)" if im
+                else "alpha=1/5, gamma=2/8"),
             "ms_per_iteration": round(ms, 3),
             "fused_ms_per_iteration": round(prof["fpbp"]["ms"] / iters, 3),
             "split_ms_per_iteration": round(ms_split, 3),

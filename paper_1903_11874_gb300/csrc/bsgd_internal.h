@@ -255,10 +255,10 @@ bsgd_status launch_fp_solve(const bsgd_geometry *g, const SolveDev &S, const voi
                             cudaStream_t st);
 bsgd_status launch_bp_solve(const bsgd_geometry *g, const SolveDev &S, bsgd_dtype st_t,
                             int max_pairs, int max_tiles, cudaStream_t st);
-// Several column blocks per iteration (2 .. kMaxFusedCols), no detector cells:
-// FP, residual and BP in one pass over the bounding box of the selected
-// blocks' bands; grid z = row-block slots (max_rows), max_tiles bounds the
-// tiles of any such box.
+// Several column blocks per iteration (2 .. kMaxFusedCols), every drawn row
+// block paired with every drawn column block: FP, residual and BP in one pass
+// over the bounding box of the selected blocks' bands; grid z = row-block
+// slots (max_rows), max_tiles bounds the tiles of any such box.
 constexpr int kMaxFusedCols = 4;
 bsgd_status launch_fpbpm_solve(const bsgd_geometry *g, const SolveDev &S, const void *x,
                                bsgd_dtype st_t, int max_rows, int max_tiles, int n_cols,

@@ -335,11 +335,13 @@ __global__ void __launch_bounds__(128) fpbp_solve_kernel(const DeviceGeom G, con
 }
 
 // FP, residual and BP of one ray in one pass when an iteration selects several
-// column blocks (at most NC) and no detector cells: the ray's new residual
-// needs the new z^j of every selected block, so the thread walks each selected
-// slab forward, forms r = y - sum_j z^j, then walks each slab back with that
-// block's own snapshot difference r - r~^j. The work item is a tile of the
-// bounding box of the selected blocks' bands (the rows the split path's
+// column blocks (at most NC) for each selected row block: the ray's new
+// residual needs the new z^j of every selected block, so the thread walks each
+// selected slab forward, forms r = y - sum_j z^j, then walks each slab back
+// with that block's own snapshot difference r - r~^j. With detector cells
+// (Algorithm 2) a block's walks are taken only by the rays of the cell drawn
+// for that pair; the others keep their z^j and r~^j. The work item is a tile
+// of the bounding box of the selected blocks' bands (the rows the split path's
 // residual pass covers) for one view of one selected row block (rs).
 template <typename T, int NC>
 __device__ __forceinline__ void fpbpm_solve_body(const DeviceGeom &G, const SolveDev &S,
@@ -371,15 +373,25 @@ __device__ __forceinline__ void fpbpm_solve_body(const DeviceGeom &G, const Solv
     T *z = reinterpret_cast<T *>(S.z);
     float zn[NC];
     int64_t kj[NC];
-    bool in[NC];
+    bool inb[NC], part[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         zn[c] = 0.f;
-        in[c] = false;
+        inb[c] = part[c] = false;
         kj[c] = 0;
         if (!act || js[c] < 0) continue;
-        kj[c] = zslot(G, js[c], a, u, v, in[c]);
-        if (!in[c]) continue;   // z^j is 0 outside block j's band
+        kj[c] = zslot(G, js[c], a, u, v, inb[c]);
+        // the ray takes part in pair (i, j) if it lies in j's band (z^j is 0
+        // outside it) and in the detector cell drawn for the pair at this view
+        // (pairs are the drawn rows x the drawn columns, row-major)
+        part[c] = inb[c];
+        if (part[c] && S.n_cells > 1) {
+            const int cell = S.cells[(rs * W.n_cols + c) * G.max_views + slot];
+            if (cell >= 0)
+                part[c] = ((cell & 1) != 0) == (u >= G.nu / 2) &&
+                          (S.n_cells != 4 || ((cell >> 1) != 0) == (v >= G.nv / 2));
+        }
+        if (!part[c]) continue;
         RayWalk w;
         if (ray_setup(G, a, u, v, G.plane_start[js[c]], G.plane_start[js[c] + 1], w, yf)) {
             float acc = 0.f;
@@ -400,7 +412,7 @@ __device__ __forceinline__ void fpbpm_solve_body(const DeviceGeom &G, const Solv
             float zv = 0.f;
 #pragma unroll
             for (int c = 0; c < NC; ++c)
-                if (jj == js[c]) {
+                if (jj == js[c] && part[c]) {
                     sel = true;
                     zv = zn[c];
                 }
@@ -426,7 +438,7 @@ __device__ __forceinline__ void fpbpm_solve_body(const DeviceGeom &G, const Solv
     T *rt = reinterpret_cast<T *>(S.rt);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        if (!act || !in[c]) continue;
+        if (!act || !part[c]) continue;
         const float dw = rn - ldv(rt + kj[c]);
         stf(rt + kj[c], rn);
         if (dw == 0.f) continue;

@@ -1371,10 +1371,9 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st, bool d
         stage_end(s, BSGD_STAGE_SAMPLE, b, 1, st);
     }
     // several column blocks fuse too when every drawn row block is paired with
-    // every drawn column block (uniform draws, not a replayed trace) and no
-    // detector cells restrict the rays of a pair
+    // every drawn column block (uniform draws, not a replayed trace)
     const bool replaying = s->replay && k >= s->replay_start && k < s->replay_start + s->replay_n;
-    const bool fuse_multi = !s->fused && s->kN <= kMaxFusedCols && s->n_cells == 1 &&
+    const bool fuse_multi = !s->fused && s->kN <= kMaxFusedCols &&
                             s->p.pair_sampling == BSGD_PAIRS_UNIFORM && !replaying;
     if (s->max_tiles > 0 && s->fused && !s->split) {
         // one column block per iteration: FP, residual and BP in one pass

@@ -250,6 +250,42 @@ def test_reduced_precision_storage(storage):
     assert rel_l2(x.float().cpu().double().numpy(), ost.x) <= 1e-2
 
 
+@pytest.mark.parametrize("kM,kN,cells", [(1, 2, B.CELLS_GEOMETRIC), (1, 4, B.CELLS_GEOMETRIC),
+                                           (2, 2, B.CELLS_UNIFORM)])
+def test_several_column_blocks_with_cells(kM, kN, cells):
+    """Algorithm 2's detector cells with several column blocks per iteration
+    (the paper's BSGD-IM set-up draws 4 of 8 column blocks): the fused pass
+    walks block j only for the rays of the cell drawn for pair (i, j). Same
+    draws and image as the split path; the oracle replaying the GPU's draws
+    gives the same image."""
+    s, og, gg, y, mu, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    iters = 2 * (M // kM) * (N // kN)
+    out = []
+    for split in (False, True):
+        prm = B.SolveParams(alpha=kM / M, gamma=kN / N, step_rule=B.STEP_FIXED, mu=mu, seed=6,
+                            cells=cells, n_cells=4)
+        st = B.State(gg, prm, torch.from_numpy(y.astype(np.float32)).to(DEV))
+        st.set_split(split)
+        x = torch.zeros(gg.n_cols, device=DEV)
+        st.profile(True)
+        st.block_step(x, iters)
+        prof = st.read_profile()
+        out.append((x.cpu().double().numpy(), st.read_trace(iters), st.query(), prof))
+    (xf, tf, qf, pf), (xs, ts, qs, ps) = out
+    assert pf["fpbp"]["launches"] == iters and ps["fp"]["launches"] == iters
+    assert np.array_equal(tf, ts)
+    assert rel_l2(xf, xs) <= 1e-6 and qf["updates"] == qs["updates"]
+    names = {B.CELLS_GEOMETRIC: "geometric", B.CELLS_UNIFORM: "uniform"}
+    po = OB.Params(M, N, kM / M, kN / N, mu, seed=6, cells=names[cells], n_cells=4)
+    sels = oracle_replay(tf, kM * kN, gg.info.max_views_per_block, M, og, po, True)
+    assert all(len(sel.pairs) == kM * kN for sel in sels)
+    ost = OB.BSGDState(og, y, po)
+    for sel in sels:
+        ost.step(sel)
+    assert rel_l2(xf, ost.x) <= 1e-5
+
+
 @pytest.mark.parametrize("storage", [B.BF16, B.F16])
 def test_reduced_precision_several_column_blocks(storage):
     """16-bit storage through the multi-block fused pass (alpha = 1/4, gamma =
