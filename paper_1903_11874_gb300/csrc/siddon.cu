@@ -401,11 +401,15 @@ __device__ __forceinline__ void fpbpm_solve_body(const DeviceGeom &G, const Solv
         stf(z + kj[c], zn[c]);
         zn[c] = rnd(zn[c], z);
     }
+    // a ray that takes part in no pair kept every z^j, so its r stands
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) any |= part[c];
     const int64_t row = act ? ((int64_t)a * G.nv + v) * G.nu + u : 0;
     T *r = reinterpret_cast<T *>(S.r);
     double dn = 0.0;
     float rn = 0.f;
-    if (act) {
+    if (act && any) {
         float zs = 0.f;
         for (int jj = 0; jj < G.N; ++jj) {   // z^jj is 0 outside block jj's band
             bool sel = false;
