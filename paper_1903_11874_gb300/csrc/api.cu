@@ -87,9 +87,8 @@ extern "C" bsgd_status bsgd_forward_project(const bsgd_geometry *g, const void *
     // projection is the same without it (only slower), so a failed allocation
     // is not an error
     void *xT = nullptr;
-    if (plain_wants_transpose(g, rows.data(), (int)rows.size()) &&
-        pool_alloc(&xT, (size_t)C * dtype_size(xt), st) != BSGD_OK)
-        xT = nullptr;
+    if (plain_wants_transpose(g, rows.data(), (int)rows.size()))
+        pool_try_alloc(&xT, (size_t)C * dtype_size(xt), st);
     auto run_all = [&]() -> bsgd_status {
         for (int b = 0; b < batch; ++b) {
             const char *xb = (const char *)x + (size_t)b * C * dtype_size(xt);
@@ -124,9 +123,8 @@ extern "C" bsgd_status bsgd_back_project(const bsgd_geometry *g, const void *r, 
     // y-fastest FP32 accumulator for the views whose rays run along x, added
     // back into x after each run (optional, as in the forward projection)
     float *gT = nullptr;
-    if (plain_wants_transpose(g, rows.data(), (int)rows.size()) &&
-        pool_alloc((void **)&gT, (size_t)C * 4, st) != BSGD_OK)
-        gT = nullptr;
+    if (plain_wants_transpose(g, rows.data(), (int)rows.size()))
+        pool_try_alloc((void **)&gT, (size_t)C * 4, st);
     auto run_all = [&]() -> bsgd_status {
         for (int b = 0; b < batch; ++b) {
             const char *rb = (const char *)r + (size_t)b * R * dtype_size(rt);

@@ -224,6 +224,8 @@ bsgd_status build_host_tables(const bsgd_geometry_desc *desc, int M, int N, bsgd
 // Device memory from the library's stream-ordered pool (solver.cu), and the
 // stream-ordered release of a solver state (serving).
 bsgd_status pool_alloc(void **p, size_t bytes, cudaStream_t st);
+// The same for optional scratch: false (and no recorded error) when it fails.
+bool pool_try_alloc(void **p, size_t bytes, cudaStream_t st);
 void pool_free(void *p, cudaStream_t st);
 void state_release(bsgd_state *s, cudaStream_t st);
 

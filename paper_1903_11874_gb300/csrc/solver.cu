@@ -821,6 +821,17 @@ static void pfree(void *p) {
 
 namespace bsgd {
 bsgd_status pool_alloc(void **p, size_t bytes, cudaStream_t st) { return palloc(p, bytes, st); }
+bool pool_try_alloc(void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    cudaMemPool_t pool = nullptr;
+    if (state_pool(&pool) != BSGD_OK) return false;
+    if (cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return true;
+}
 void pool_free(void *p, cudaStream_t st) {
     if (p) cudaFreeAsync(p, st);
 }
@@ -912,7 +923,7 @@ bsgd_status power_iteration(const bsgd_geometry *g, int j, int iters, const int 
     // y-fastest copies of v and of the BP accumulator for the views whose rays
     // run along x (optional: without them the iteration is the same, slower)
     if (plain_wants_transpose(g, row_ids, n_rb) &&
-        (palloc((void **)&vT, n * 4, st) != BSGD_OK || palloc((void **)&wT, n * 4, st) != BSGD_OK)) {
+        (!pool_try_alloc((void **)&vT, n * 4, st) || !pool_try_alloc((void **)&wT, n * 4, st))) {
         pool_free(vT, st);
         pool_free(wT, st);
         vT = wT = nullptr;
