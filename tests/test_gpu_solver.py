@@ -250,6 +250,27 @@ def test_reduced_precision_storage(storage):
     assert rel_l2(x.float().cpu().double().numpy(), ost.x) <= 1e-2
 
 
+def test_switching_between_fused_and_split_passes():
+    """One state alternates the multi-block fused pass and the split passes
+    between block_step calls (they share z, r~, r, S and the draws): the
+    trajectory is the oracle's."""
+    s, og, gg, y, mu, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    prm = B.SolveParams(alpha=1 / M, gamma=2 / N, step_rule=B.STEP_FIXED, mu=mu, seed=12)
+    st = B.State(gg, prm, torch.from_numpy(y.astype(np.float32)).to(DEV))
+    x = torch.zeros(gg.n_cols, device=DEV)
+    st.profile(True)
+    for split in (False, True, False, True):
+        st.set_split(split)
+        st.block_step(x, 5)
+    torch.cuda.synchronize()
+    prof = st.read_profile()
+    assert prof["fpbp"]["launches"] == 10 and prof["fp"]["launches"] == 10
+    ost = OB.bsgd(og, y, OB.Params(M, N, 1 / M, 2 / N, mu, seed=12), 20)
+    assert rel_l2(x.cpu().double().numpy(), ost.x) <= 1e-5
+    assert abs(st.query()["residual_norm"] - ost.residual_norm()) <= 1e-4 * np.linalg.norm(y)
+
+
 @pytest.mark.parametrize("kM,kN,cells", [(1, 2, B.CELLS_GEOMETRIC), (1, 4, B.CELLS_GEOMETRIC),
                                            (2, 2, B.CELLS_UNIFORM)])
 def test_several_column_blocks_with_cells(kM, kN, cells):
