@@ -346,8 +346,8 @@ typedef enum {
     BSGD_STAGE_BP = 3,       /* back projection of the residual change        */
     BSGD_STAGE_UPDATE = 4,   /* x_J += mu g_J                                 */
     BSGD_STAGE_TV = 5,       /* TV proximal step (BSGD-TV)                    */
-    BSGD_STAGE_FPBP = 6,     /* FP, residual and BP in one kernel (one column
-                                block per iteration)                          */
+    BSGD_STAGE_FPBP = 6,     /* FP, residual and BP in one kernel (1 to 4
+                                column blocks per iteration)                  */
     BSGD_N_STAGES = 7
 } bsgd_stage;
 
@@ -370,8 +370,10 @@ bsgd_status bsgd_state_profile(bsgd_state *s, int enable);
 bsgd_status bsgd_state_set_sampling(bsgd_state *s, int pair_sampling, int cells, int n_cells,
                                     void *stream);
 
-/* split = 1: run FP and BP as two kernels even with one column block per
- * iteration (to time them apart); default 0 (one fused kernel). */
+/* split = 1: run FP, the residual (with several column blocks per iteration)
+ * and BP as separate kernels (to time them apart); default 0: one fused kernel
+ * when 1 to 4 column blocks are drawn per iteration (with 2 to 4: uniform
+ * pair draws, not a replayed trace), separate kernels otherwise. */
 bsgd_status bsgd_state_set_split(bsgd_state *s, int split);
 bsgd_status bsgd_state_read_profile(bsgd_state *s, bsgd_profile *out, void *stream);
 
