@@ -378,6 +378,29 @@ bsgd_status bsgd_state_set_split(bsgd_state *s, int split);
 bsgd_status bsgd_state_read_profile(bsgd_state *s, bsgd_profile *out, void *stream);
 
 /*
+ * Checkpoint / resume. The paper has no such facility; it follows from the
+ * state being (z^j, r~^j, r, the FP64 residual table, g, mu, the iteration
+ * counter, the update counter, the 16-bit image's low-order term, Algorithm 3's
+ * window state and the sampling trace) and from every draw being a function of
+ * (seed, iteration), so a resumed run takes the same draws as an
+ * uninterrupted one.
+ * bsgd_state_checkpoint_bytes: size of the checkpoint of s.
+ * bsgd_state_save: copies it into host memory `host` of `cap` bytes
+ *   (cap >= bsgd_state_checkpoint_bytes); synchronises `stream`. y and x are
+ *   not part of it: the caller keeps x (as it was at the save) and y.
+ * bsgd_state_restore: loads a checkpoint into s, a state created from the same
+ *   geometry, parameters and y (a fresh one, or the same one to roll back);
+ *   continue with bsgd_block_step and the x of the save. Restores the
+ *   sampling mode the saved state ran with (bsgd_state_set_sampling).
+ *   Synchronises `stream`. Errors: INVALID_ARG when the blob is not a
+ *   checkpoint of a state of this geometry, block counts, pair counts and
+ *   storage type, or is truncated.
+ */
+bsgd_status bsgd_state_checkpoint_bytes(const bsgd_state *s, int64_t *bytes);
+bsgd_status bsgd_state_save(bsgd_state *s, void *host, int64_t cap, void *stream);
+bsgd_status bsgd_state_restore(bsgd_state *s, const void *host, int64_t bytes, void *stream);
+
+/*
  * One-call reconstruction: state_create, epochs * 1/(alpha*gamma) iterations,
  * query, destroy. y and x may be host or device pointers (host buffers are
  * copied in and out inside the call). x holds x0 = 0 on entry and the

@@ -27,7 +27,8 @@ EXPORTS = (
     "bsgd_count_updates_noalloc", "bsgd_power_iteration", "bsgd_tv_prox", "bsgd_state_create", "bsgd_state_destroy",
     "bsgd_block_step", "bsgd_state_query", "bsgd_trace_stride", "bsgd_state_read_trace",
     "bsgd_state_set_replay", "bsgd_state_profile", "bsgd_state_read_profile",
-    "bsgd_state_set_split", "bsgd_state_set_sampling", "bsgd_solve",
+    "bsgd_state_set_split", "bsgd_state_set_sampling", "bsgd_state_checkpoint_bytes",
+    "bsgd_state_save", "bsgd_state_restore", "bsgd_solve",
     "bsgd_request_bytes", "bsgd_server_create", "bsgd_server_destroy", "bsgd_server_submit",
     "bsgd_server_wait", "bsgd_server_poll", "bsgd_server_get_stats",
 )
@@ -158,6 +159,9 @@ def load(build_if_missing: bool = True):
         "bsgd_state_set_replay": (st, [_vp, _i32p, ctypes.c_int64]),
         "bsgd_state_profile": (st, [_vp, ctypes.c_int]),
         "bsgd_state_set_split": (st, [_vp, ctypes.c_int]),
+        "bsgd_state_checkpoint_bytes": (st, [_vp, P(ctypes.c_int64)]),
+        "bsgd_state_save": (st, [_vp, _vp, ctypes.c_int64, _vp]),
+        "bsgd_state_restore": (st, [_vp, _vp, ctypes.c_int64, _vp]),
         "bsgd_state_set_sampling": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
         "bsgd_state_read_profile": (st, [_vp, P(Profile), _vp]),
         "bsgd_solve": (st, [_vp, P(SolveParamsC), _vp, st, _vp, st, P(Report), _vp]),
@@ -420,6 +424,20 @@ class State:
     @property
     def trace_stride(self) -> int:
         return int(load().bsgd_trace_stride(self.handle))
+
+    def save(self, stream=None) -> bytes:
+        """Checkpoint of the state (bsgd_state_save); x and y are not in it."""
+        n = ctypes.c_int64(0)
+        _check(load().bsgd_state_checkpoint_bytes(self.handle, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(max(1, n.value))
+        _check(load().bsgd_state_save(self.handle, ctypes.cast(buf, _vp), n.value, _stream(stream)))
+        return buf.raw[: n.value]
+
+    def restore(self, blob: bytes, stream=None):
+        """Load a checkpoint of a state with the same geometry, parameters and y
+        (bsgd_state_restore); continue with the x of the save."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        _check(load().bsgd_state_restore(self.handle, ctypes.cast(buf, _vp), len(blob), _stream(stream)))
 
     def read_trace(self, n_iters, stream=None) -> np.ndarray:
         s = self.trace_stride

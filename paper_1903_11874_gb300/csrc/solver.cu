@@ -1535,6 +1535,138 @@ extern "C" bsgd_status bsgd_state_set_split(bsgd_state *s, int split) {
     return BSGD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: a header that identifies the state's shape, then the
+// device arrays in a fixed order.
+
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    int32_t version, storage;
+    int32_t kind, M, N, kM, kN, P;
+    int32_t pair_sampling, cells, n_cells, auto_mu, has_tv, pad;
+    int64_t nx, ny, nz, n_views, nu, nv;
+    int64_t iters, trace_rows, payload;
+    uint64_t seed;
+};
+constexpr char kCkptMagic[8] = {'B', 'S', 'G', 'D', 'C', 'K', 'P', 'T'};
+
+struct CkptPart {
+    void *dev;
+    size_t bytes;
+};
+
+// The device arrays of a checkpoint, in blob order; trace rows = iterations
+// recorded so far.
+std::vector<CkptPart> ckpt_parts(const bsgd_state *s, int64_t trace_rows) {
+    const bsgd_geometry *g = s->g;
+    const size_t es = dtype_size(s->st), R = (size_t)g->n_rows(), C = (size_t)g->n_cols();
+    const size_t Z = (size_t)g->zlen;
+    std::vector<CkptPart> v = {
+        {s->z, Z * es}, {s->rt, Z * es}, {s->r, R * es}, {s->grad, C * 4},
+        {s->S, 8 * (size_t)g->M * g->desc.nv}, {s->d_mu, 8}, {s->d_iter, 8}, {s->updates, 8},
+        {s->trace, 4 * (size_t)trace_rows * s->stride}};
+    if (s->gT) v.push_back({s->gT, C * 4});
+    if (s->xlo) v.push_back({s->xlo, C * es});
+    if (s->eud) {
+        v.push_back({s->eud, 8 * C});
+        v.push_back({s->eud_prev, 8 * C});
+        v.push_back({s->am, sizeof(AutoMuHist)});
+    }
+    return v;
+}
+
+CkptHeader ckpt_header(const bsgd_state *s) {
+    const bsgd_geometry *g = s->g;
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.storage = s->st;
+    h.kind = g->desc.kind;
+    h.M = g->M;
+    h.N = g->N;
+    h.kM = s->kM;
+    h.kN = s->kN;
+    h.P = s->P;
+    h.pair_sampling = s->p.pair_sampling;
+    h.cells = s->p.cells;
+    h.n_cells = s->n_cells;
+    h.auto_mu = s->eud != nullptr;
+    h.has_tv = s->p.tv_lambda > 0;
+    h.nx = g->desc.nx, h.ny = g->desc.ny, h.nz = g->desc.nz;
+    h.n_views = g->desc.n_views, h.nu = g->desc.nu, h.nv = g->desc.nv;
+    h.iters = s->iters;
+    h.trace_rows = std::min(s->iters, s->trace_cap);
+    h.seed = s->p.seed;
+    size_t tot = 0;
+    for (const CkptPart &q : ckpt_parts(s, h.trace_rows)) tot += q.bytes;
+    h.payload = (int64_t)tot;
+    return h;
+}
+
+}  // namespace
+
+extern "C" bsgd_status bsgd_state_checkpoint_bytes(const bsgd_state *s, int64_t *bytes) {
+    if (!s || !bytes) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    *bytes = (int64_t)sizeof(CkptHeader) + ckpt_header(s).payload;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_state_save(bsgd_state *s, void *host, int64_t cap, void *stream) {
+    if (!s || !host) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    const CkptHeader h = ckpt_header(s);
+    if (cap < (int64_t)sizeof(CkptHeader) + h.payload)
+        return fail(BSGD_ERR_INVALID_ARG, "checkpoint buffer too small");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *out = static_cast<char *>(host);
+    std::memcpy(out, &h, sizeof h);
+    size_t off = sizeof h;
+    for (const CkptPart &q : ckpt_parts(s, h.trace_rows)) {
+        if (q.bytes) BSGD_CUDA(cudaMemcpyAsync(out + off, q.dev, q.bytes, cudaMemcpyDeviceToHost, st));
+        off += q.bytes;
+    }
+    BSGD_CUDA(cudaStreamSynchronize(st));
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_state_restore(bsgd_state *s, const void *host, int64_t bytes,
+                                          void *stream) {
+    if (!s || !host) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (bytes < (int64_t)sizeof(CkptHeader)) return fail(BSGD_ERR_INVALID_ARG, "checkpoint truncated");
+    CkptHeader h;
+    std::memcpy(&h, host, sizeof h);
+    const CkptHeader mine = ckpt_header(s);
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+        return fail(BSGD_ERR_INVALID_ARG, "not a BSGD checkpoint");
+    if (h.storage != mine.storage || h.kind != mine.kind || h.M != mine.M || h.N != mine.N ||
+        h.kM != mine.kM || h.kN != mine.kN || h.P != mine.P || h.auto_mu != mine.auto_mu ||
+        h.has_tv != mine.has_tv || h.nx != mine.nx || h.ny != mine.ny || h.nz != mine.nz ||
+        h.n_views != mine.n_views || h.nu != mine.nu || h.nv != mine.nv || h.seed != mine.seed)
+        return fail(BSGD_ERR_INVALID_ARG, "checkpoint of a different geometry or solver set-up");
+    if (h.iters < 0 || h.trace_rows != std::min(h.iters, s->trace_cap))
+        return fail(BSGD_ERR_INVALID_ARG, "corrupt checkpoint header");
+    const std::vector<CkptPart> parts = ckpt_parts(s, h.trace_rows);
+    size_t need = 0;
+    for (const CkptPart &q : parts) need += q.bytes;
+    if ((int64_t)need != h.payload || bytes < (int64_t)sizeof(CkptHeader) + h.payload)
+        return fail(BSGD_ERR_INVALID_ARG, "checkpoint truncated");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h.pair_sampling != s->p.pair_sampling || h.cells != s->p.cells || h.n_cells != s->n_cells)
+        BSGD_TRY(bsgd_state_set_sampling(s, h.pair_sampling, h.cells, h.n_cells, stream));
+    const char *in = static_cast<const char *>(host) + sizeof h;
+    for (const CkptPart &q : parts) {
+        if (q.bytes) BSGD_CUDA(cudaMemcpyAsync(q.dev, in, q.bytes, cudaMemcpyHostToDevice, st));
+        in += q.bytes;
+    }
+    BSGD_CUDA(cudaStreamSynchronize(st));
+    s->iters = h.iters;
+    cudaFree(s->replay);   // a replay in progress belongs to the state that was replaced
+    s->replay = nullptr;
+    s->replay_n = 0;
+    return BSGD_OK;
+}
+
 extern "C" bsgd_status bsgd_state_read_profile(bsgd_state *s, bsgd_profile *out, void *stream) {
     if (!s || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
     BSGD_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
