@@ -291,6 +291,7 @@ struct SampleArgs {
     int64_t trace_cap;
     int stride;
     const unsigned long long *counts;  // N x n_views x n_cells
+    const unsigned long long *pair_upd;  // M x N updates of whole views (null: sum per view)
     unsigned long long *updates;
 };
 

@@ -127,6 +127,10 @@ __device__ void sample_body(const SampleArgs &A) {
         const int nS = G.M * G.nv;
         const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
         const bool staged = nS <= kSampleSmemS;
+        // the first batch of band limits is fetched with the staging loads
+        const int kl0 = warp + lane * nwarps;
+        const int lo0 = kl0 < MN ? A.wband[2 * kl0] : 0;
+        const int hi0 = kl0 < MN ? A.wband[2 * kl0 + 1] : -1;
         if (staged) {
 #pragma unroll 8
             for (int k = tid; k < nS; k += blockDim.x) s_S[k] = A.S[k];
@@ -138,8 +142,8 @@ __device__ void sample_body(const SampleArgs &A) {
         // lane and handed round by shuffles
         for (int k0 = warp; k0 < MN; k0 += 32 * nwarps) {
             const int kl = k0 + lane * nwarps;
-            const int lo_l = kl < MN ? A.wband[2 * kl] : 0;
-            const int hi_l = kl < MN ? A.wband[2 * kl + 1] : -1;
+            const int lo_l = k0 == warp ? lo0 : (kl < MN ? A.wband[2 * kl] : 0);
+            const int hi_l = k0 == warp ? hi0 : (kl < MN ? A.wband[2 * kl + 1] : -1);
             for (int t = 0; t < 32 && k0 + t * nwarps < MN; ++t) {
                 const int k = k0 + t * nwarps;
                 const int lo = __shfl_sync(0xffffffffu, lo_l, t), hi = __shfl_sync(0xffffffffu, hi_l, t);
@@ -192,9 +196,17 @@ __device__ void sample_body(const SampleArgs &A) {
     __syncthreads();
     const int np = s_np;
     // cells: one per view of each pair's row block; voxel-ray updates of the
-    // chosen rows (FP + BP) summed in parallel
+    // chosen rows (FP + BP) summed in parallel (whole views: one table entry
+    // per pair)
     unsigned long long upd = 0;
+    const bool whole = A.cells_mode == BSGD_CELLS_NONE && A.pair_upd != nullptr;
+    if (whole && tid == 0)
+        for (int p = 0; p < np; ++p) upd += A.pair_upd[s_pi[p] * G.N + s_pj[p]];
     for (int q = tid; q < np * G.max_views; q += blockDim.x) {
+        if (whole) {
+            A.cells[q] = -1;
+            continue;
+        }
         const int p = q / G.max_views, k = q % G.max_views;
         const int i = s_pi[p], j = s_pj[p];
         const int nvb = G.block_nviews[i];
@@ -258,6 +270,22 @@ __device__ void sample_body(const SampleArgs &A) {
 }
 
 __global__ void __launch_bounds__(kSampleThreads) sample_kernel(const SampleArgs A) { sample_body(A); }
+
+// pair_upd[i][j] = voxel-ray updates of every whole view of row block i in
+// column block j (the cell counts summed).
+__global__ void pair_updates_kernel(const DeviceGeom G, const unsigned long long *__restrict__ counts,
+                                    int n_cells, unsigned long long *__restrict__ out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= G.M * G.N) return;
+    const int i = q / G.N, j = q % G.N;
+    unsigned long long t = 0;
+    for (int k = 0; k < G.block_nviews[i]; ++k) {
+        const unsigned long long *cn =
+            counts + ((size_t)j * G.n_views + G.block_views[i * G.max_views + k]) * n_cells;
+        for (int c = 0; c < n_cells; ++c) t += cn[c];
+    }
+    out[q] = t;
+}
 
 // r = y - sum_j z^j over the rows of the selected row blocks that the
 // iteration's FPs changed (the union of the selected column blocks' bands in
@@ -725,6 +753,7 @@ struct bsgd_state {
     int32_t *trace = nullptr, *replay = nullptr;
     int64_t replay_start = 0, replay_n = 0;
     unsigned long long *counts = nullptr, *updates = nullptr;
+    unsigned long long *pair_upd = nullptr;   // M x N whole-view update counts
     // Algorithm 3
     int auto_win = 0;            // epochs per test (0: off)
     double *eud = nullptr, *eud_prev = nullptr, *am_part = nullptr;
@@ -841,7 +870,7 @@ static void free_state(bsgd_state *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     // counts and cw belong to the geometry's cache; replay is a plain allocation
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->trace, s->updates, s->eud,
+                    s->wband, s->d_iter, s->trace, s->updates, s->pair_upd, s->eud,
                     s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) pfree(p);
     cudaFree(s->replay);
@@ -1124,6 +1153,7 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         (e = palloc((void **)&s->d_iter, 8, st)) ||
         (e = palloc((void **)&s->trace, 4 * (size_t)s->trace_cap * s->stride, st)) ||
         (e = palloc((void **)&s->updates, 8, st)) ||
+        (e = palloc((void **)&s->pair_upd, 8 * (size_t)M * N, st)) ||
         (s->st != BSGD_F32 && (e = palloc(&s->xlo, C * es, st))) ||
         (g->desc.nz > 1 && (e = palloc(&s->xT, C * es, st))) ||
         (g->desc.nz > 1 && (e = palloc((void **)&s->gT, C * 4, st))) ||
@@ -1153,6 +1183,8 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
                                   cudaMemcpyHostToDevice, st));
         BSGD_TRY(norm_table(g, s->r, s->st, s->S, st));
         BSGD_TRY(geometry_tables(g, s->n_cells, p->cells == BSGD_CELLS_GEOMETRIC, st, &s->counts, &s->cw));
+        pair_updates_kernel<<<(M * N + 127) / 128, 128, 0, st>>>(g->dg, s->counts, s->n_cells, s->pair_upd);
+        BSGD_CUDA(cudaGetLastError());
         // step size
         if (p->step_rule == BSGD_STEP_FIXED) {
             s->mu = p->mu;
@@ -1230,7 +1262,7 @@ void state_release(bsgd_state *s, cudaStream_t st) {
     }
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->trace, s->updates, s->eud,
+                    s->wband, s->d_iter, s->trace, s->updates, s->pair_upd, s->eud,
                     s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) pool_free(p, st);
     delete s;
@@ -1276,6 +1308,7 @@ static void fill_sample_args(const bsgd_state *s, SampleArgs &A, int64_t k) {
     A.trace_cap = s->trace_cap;
     A.stride = s->stride;
     A.counts = s->counts;
+    A.pair_upd = s->pair_upd;
     A.updates = s->updates;
 }
 
@@ -1526,6 +1559,9 @@ extern "C" bsgd_status bsgd_state_set_sampling(bsgd_state *s, int pair_sampling,
     s->counts = counts;
     s->cw = cw;
     s->dev.n_cells = nc;
+    pair_updates_kernel<<<(g->M * g->N + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+        g->dg, counts, nc, s->pair_upd);
+    BSGD_CUDA(cudaGetLastError());
     return BSGD_OK;
 }
 

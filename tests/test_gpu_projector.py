@@ -182,3 +182,26 @@ def test_config2_sampled_rays_and_voxels():
     # corner: ~6e-8 * 630 ~ 4e-5 voxel), and the signed terms do not telescope,
     # so rel-L2 ~ 4e-5 / (mean segment ~0.7) ~ 6e-5; bound 1e-4
     assert rel_l2(gotb, refb) < 1e-4
+
+
+def test_fp_is_deterministic_and_bp_within_rounding():
+    """The FP of a ray is one thread's fixed-order sum: two runs agree bit for
+    bit (also through the solver's fused pass). The BP scatters with float
+    atomics whose order varies: two runs agree to FP32 rounding."""
+    s = spec("cone_small")
+    gg = gpu_geom(s)
+    x = _cuda(synth.uniform_array(gg.n_cols, 31))
+    r = _cuda(synth.normal_array(gg.n_rows, 32))
+    ys = []
+    for _ in range(2):
+        y = torch.zeros(gg.n_rows, device=DEV)
+        B.bsgd_forward_project(gg, x, y)
+        ys.append(y)
+    assert torch.equal(ys[0], ys[1])
+    bs = []
+    for _ in range(2):
+        b = torch.zeros(gg.n_cols, device=DEV)
+        B.bsgd_back_project(gg, r, b)
+        bs.append(b.double())
+    scale = float(bs[0].abs().max())
+    assert float((bs[0] - bs[1]).abs().max()) <= 1e-5 * scale
