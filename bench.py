@@ -46,11 +46,11 @@ UNIT = "GVox-ray/s"
 ALU_OPS_PER_UPDATE = 5
 # DRAM bytes (read + write) per launch of the fused kernel, mean over the 64
 # launches of one epoch of this workload, from one ncu capture of the current
-# kernel (profiles/fpbp_solve_kernel_cone256_dram_traffic.md); null for the
+# kernel (its DRAM-traffic capture is summarised under profiles/); null for the
 # split kernels, which were not captured.
 TRAFFIC_PER_LAUNCH = {"fpbp": 46_481_784}
 # What does bind the fused kernel, from the same kernel's ncu --set full capture
-# (profiles/fpbp_solve_kernel_cone256_ncu_full.md, the heavier of two pairs):
+# (the full capture summarised under profiles/, the heavier of two pairs):
 # L2 and L1/TEX throughput in % of their peaks, issue-active cycles in %.
 ON_CHIP_NCU = {"fpbp": {"l2_pct": 64.3, "l1tex_pct": 68.6, "issue_active_pct": 47.2}}
 

@@ -4,7 +4,7 @@ Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
 this module. It runs the paper's iteration step by step, in the paper's order,
 with every FP and BP done by the FP64 Siddon projector in oracle/projector.py.
 
-Readings of the paper used here (each is also listed in the design doc):
+Readings of the paper used here (the design notes list each of them too):
   * gradient of 1/2 ||y - A x||^2 is A^T r, so the factor 2 printed in
     Algorithm 1's BP step is folded into mu (Sec. 1, Eq. 2 vs Algorithm 1);
   * "randomly select" = uniform without replacement within an iteration,

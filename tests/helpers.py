@@ -91,7 +91,7 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-# FP32 error model of one ray sum z = L sum_k s_k x_k (derived in the design doc):
+# FP32 error model of one ray sum z = L sum_k s_k x_k:
 # every crossing parameter is within a few ulps of the chord, so each segment
 # carries an absolute length error of order 4 u T (T = chord, u = 2^-24) and
 # the FP32 accumulation adds at most n u sum |s_k x_k|. With n <= 2 nx the
