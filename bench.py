@@ -400,8 +400,11 @@ AUTOGRAD_GEOM = dict(kind="cone3d", nx=128, ny=128, nz=128, dx=1.0, dy=1.0, dz=1
 AUTOGRAD_BATCH = 16
 
 
-def epoch_rate(B, torch, dev, gg, y, prm, warm=2, epochs=3):
-    """(GVox-ray/s, profile) of whole epochs of a fresh state."""
+def epoch_rate(B, torch, dev, gg, y, prm, warm=2, epochs=3, profile=False):
+    """(GVox-ray/s, profile or None, ms per epoch) of whole epochs of a fresh
+    state, timed without per-stage events; with profile, the same number of
+    further epochs with an event pair around every launch give the stage
+    times."""
     st = B.State(gg, prm, y)
     x = torch.zeros(gg.n_cols, device=dev,
                     dtype={B.F32: torch.float32, B.BF16: torch.bfloat16, B.F16: torch.float16}[prm.storage])
@@ -409,16 +412,20 @@ def epoch_rate(B, torch, dev, gg, y, prm, warm=2, epochs=3):
         st.block_step(x, ITERS_PER_EPOCH)
     torch.cuda.synchronize()
     q0 = st.query()
-    st.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(epochs):
         st.block_step(x, ITERS_PER_EPOCH)
     e1.record()
     torch.cuda.synchronize()
-    prof = st.read_profile()
     ms = e0.elapsed_time(e1)
     upd = st.query()["updates"] - q0["updates"]
+    prof = None
+    if profile:
+        st.profile(True)
+        for _ in range(epochs):
+            st.block_step(x, ITERS_PER_EPOCH)
+        prof = st.read_profile()
     st.close()
     return upd / (ms * 1e-3) / 1e9, prof, ms / epochs
 
@@ -475,13 +482,25 @@ def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks):
                           pair_sampling=B.PAIRS_RESIDUAL, storage=B.BF16, seed=1)
     v16, _, ms16 = epoch_rate(B, torch, dev, gg, y, prm16)
     out["P_bf16_storage"] = {"value": round(v16, 3), "unit": UNIT, "ms_per_epoch": round(ms16, 3)}
+    # NEXT-1: Algorithm 3 on (a test at the end of every epoch: FP64 EUD
+    # accumulation in the update, a reduction and the decision on the device)
+    # against the same epochs with a fixed step
+    prm32 = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu,
+                          pair_sampling=B.PAIRS_RESIDUAL, seed=1)
+    v32, _, ms32 = epoch_rate(B, torch, dev, gg, y, prm32)
+    prmam = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu,
+                          pair_sampling=B.PAIRS_RESIDUAL, auto_mu=True, auto_window=1, seed=1)
+    vam, _, msam = epoch_rate(B, torch, dev, gg, y, prmam)
+    out["NEXT1_auto_mu"] = {"value": round(vam, 3), "unit": UNIT, "ms_per_epoch": round(msam, 3),
+                            "fixed_step_value": round(v32, 3),
+                            "overhead_pct": round(100.0 * (v32 / vam - 1.0), 2), "window_epochs": 1}
     # a9: TV prox (FGP, 20 iterations) once per epoch; algorithmic bytes: 72 B
     # per voxel and FGP iteration (primal: b, r_xyz read, u written; dual: u,
     # r_xyz, p_xyz read, p_xyz, r_xyz written) + 80 B per voxel for the set-up
     # and the final primal (the float4 layout of the dual fields moves ~100 B)
     prmtv = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu,
                           pair_sampling=B.PAIRS_RESIDUAL, tv_lambda=1e-3, tv_iters=20, seed=1)
-    _, ptv, _ = epoch_rate(B, torch, dev, gg, y, prmtv, warm=1, epochs=2)
+    _, ptv, _ = epoch_rate(B, torch, dev, gg, y, prmtv, warm=1, epochs=2, profile=True)
     ms_tv = ptv["tv"]["ms"] / max(1, ptv["tv"]["launches"] // 43)
     btv = gg.n_cols * (72 * 20 + 80)
     out["a9_tv_prox"] = {"ms_per_prox": round(ms_tv, 3), "bytes_per_prox": btv,
@@ -539,7 +558,6 @@ def precision_leg(B, torch, dev, epochs=2):
         st = B.State(gg, prm, y)
         lam = st.query()["mu"]            # the same step for both runs
         x = torch.zeros(gg.n_cols, device=dev, dtype=tdt)
-        st.profile(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(epochs):
@@ -547,11 +565,14 @@ def precision_leg(B, torch, dev, epochs=2):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / epochs
-        prof = st.read_profile()
         q = st.query()
-        xs[name] = x.float()
+        xs[name] = x.float().clone()
+        # one more epoch with per-stage events for the TV prox's share
+        st.profile(True)
+        st.block_step(x, 256)
+        prof = st.read_profile()
         out[name] = {"ms_per_epoch": round(ms, 2), "value": round(q["updates"] / epochs / (ms * 1e-3) / 1e9, 3),
-                     "unit": UNIT, "tv_ms_per_epoch": round(prof["tv"]["ms"] / epochs, 2),
+                     "unit": UNIT, "tv_ms_per_epoch": round(prof["tv"]["ms"], 2),
                      "residual_norm": q["residual_norm"]}
         st.close()
     d = float(torch.linalg.vector_norm(xs["bf16"] - xs["fp32"]) / torch.linalg.vector_norm(xs["fp32"]))
