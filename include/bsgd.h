@@ -424,8 +424,9 @@ bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_params *p,
  * and budget free up; finished requests leave without stopping the others.
  * Each request's result equals its result alone up to the order of float
  * atomics (its sampling depends only on its own seed and iteration count).
- * Requests must draw one column block per iteration (gamma N = 1) and use no TV
- * prox; others are rejected at submit.
+ * Requests may draw up to 4 column blocks per iteration (gamma N <= 4; with
+ * more than one, uniform pairs), and use no TV prox and no automatic step;
+ * others are rejected at submit.
  */
 typedef struct bsgd_server bsgd_server;
 
@@ -462,7 +463,7 @@ bsgd_status bsgd_server_destroy(bsgd_server *s);
  * Queue a reconstruction: y (host, n_rows elements of type yt) is copied before
  * the call returns; the result (n_cols float32 values) is written to x_out
  * (host, caller-owned, valid until the request completes or fails).
- * Errors: INVALID_ARG (bad geometry / params, gamma N != 1, TV), BUDGET (the
+ * Errors: INVALID_ARG (bad geometry / params, gamma N > 4, TV), BUDGET (the
  * request alone exceeds the budget), STATE (server stopping).
  */
 bsgd_status bsgd_server_submit(bsgd_server *s, const bsgd_geometry_desc *desc, int M, int N,

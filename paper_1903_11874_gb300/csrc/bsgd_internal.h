@@ -305,11 +305,11 @@ struct ReqDesc {
     void *x;                 // image (storage type)
     void *xlo;               // low-order image term (16-bit storage) or null
     int dtype;               // storage type
-    int max_tiles;           // detector tiles of the largest band of one pair
+    int max_tiles;           // detector tiles of the largest work box of one view
     int active;
-    int pad;
+    int kN;                  // column blocks per iteration (1: one-block fused pass)
     int64_t work_begin;      // first FP / BP work item of this request in a round
-    int64_t work_count;      // max_tiles * max_views * pairs
+    int64_t work_count;      // max_tiles * max_views * (pairs, or row blocks when kN > 1)
     int64_t max_block_cols;  // voxels of the largest column block
 };
 

@@ -587,7 +587,9 @@ extern "C" bsgd_status bsgd_server_submit(bsgd_server *S, const bsgd_geometry_de
     size_t bytes = 0;
     BSGD_TRY(bsgd_request_bytes(desc, M, N, p, &bytes));
     const int kN = std::max(1, (int)std::lround(p->gamma * N));
-    if (kN != 1) return fail(BSGD_ERR_INVALID_ARG, "serving needs gamma * N == 1");
+    if (kN > kMaxFusedCols) return fail(BSGD_ERR_INVALID_ARG, "serving needs gamma * N <= 4");
+    if (kN > 1 && p->pair_sampling != BSGD_PAIRS_UNIFORM)
+        return fail(BSGD_ERR_INVALID_ARG, "serving with several column blocks needs uniform pairs");
     if (p->tv_lambda > 0) return fail(BSGD_ERR_INVALID_ARG, "serving runs no TV prox");
     if (p->auto_mu) return fail(BSGD_ERR_INVALID_ARG, "serving runs no automatic step length");
     if (p->epochs < 1) return fail(BSGD_ERR_INVALID_ARG, "epochs must be >= 1");

@@ -499,13 +499,29 @@ __global__ void __launch_bounds__(128) round_solve_kernel(const ReqDesc *__restr
         const int slot = (int)(local % q.G.max_views);
         local /= q.G.max_views;
         const int tile = (int)(local % q.max_tiles);
-        const int p = (int)(local / q.max_tiles);
-        if (q.dtype == BSGD_F32)
-            fpbp_solve_body<float>(q.G, q.S, (const float *)q.x, tile, slot, p);
-        else if (q.dtype == BSGD_BF16)
-            fpbp_solve_body<__nv_bfloat16>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
-        else
-            fpbp_solve_body<__half>(q.G, q.S, (const __half *)q.x, tile, slot, p);
+        const int p = (int)(local / q.max_tiles);   // pair (one block) or row-block slot
+        if (q.kN == 1) {
+            if (q.dtype == BSGD_F32)
+                fpbp_solve_body<float>(q.G, q.S, (const float *)q.x, tile, slot, p);
+            else if (q.dtype == BSGD_BF16)
+                fpbp_solve_body<__nv_bfloat16>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
+            else
+                fpbp_solve_body<__half>(q.G, q.S, (const __half *)q.x, tile, slot, p);
+        } else if (q.kN <= 2) {
+            if (q.dtype == BSGD_F32)
+                fpbpm_solve_body<float, 2>(q.G, q.S, (const float *)q.x, tile, slot, p);
+            else if (q.dtype == BSGD_BF16)
+                fpbpm_solve_body<__nv_bfloat16, 2>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
+            else
+                fpbpm_solve_body<__half, 2>(q.G, q.S, (const __half *)q.x, tile, slot, p);
+        } else {
+            if (q.dtype == BSGD_F32)
+                fpbpm_solve_body<float, 4>(q.G, q.S, (const float *)q.x, tile, slot, p);
+            else if (q.dtype == BSGD_BF16)
+                fpbpm_solve_body<__nv_bfloat16, 4>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
+            else
+                fpbpm_solve_body<__half, 4>(q.G, q.S, (const __half *)q.x, tile, slot, p);
+        }
     }
 }
 

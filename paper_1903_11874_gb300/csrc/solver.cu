@@ -503,13 +503,15 @@ __global__ void __launch_bounds__(256) round_update_kernel(const ReqDesc *__rest
     const int r = blockIdx.y;
     if (r >= C->n || !T[r].active) return;
     const ReqDesc &q = T[r];
-    if (q.dtype == BSGD_F32)
-        update_body<float>(q.G, q.S, (float *)q.x, nullptr, 0, blockIdx.x, gridDim.x);
-    else if (q.dtype == BSGD_BF16)
-        update_body<__nv_bfloat16>(q.G, q.S, (__nv_bfloat16 *)q.x, (__nv_bfloat16 *)q.xlo, 0,
-                                   blockIdx.x, gridDim.x);
-    else
-        update_body<__half>(q.G, q.S, (__half *)q.x, (__half *)q.xlo, 0, blockIdx.x, gridDim.x);
+    for (int c = 0; c < q.kN; ++c) {   // every drawn column block
+        if (q.dtype == BSGD_F32)
+            update_body<float>(q.G, q.S, (float *)q.x, nullptr, c, blockIdx.x, gridDim.x);
+        else if (q.dtype == BSGD_BF16)
+            update_body<__nv_bfloat16>(q.G, q.S, (__nv_bfloat16 *)q.x, (__nv_bfloat16 *)q.xlo, c,
+                                       blockIdx.x, gridDim.x);
+        else
+            update_body<__half>(q.G, q.S, (__half *)q.x, (__half *)q.xlo, c, blockIdx.x, gridDim.x);
+    }
 }
 
 bsgd_status launch_round_sample(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
@@ -1316,7 +1318,8 @@ namespace bsgd {
 
 bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out) {
     if (!s || !x || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
-    if (!s->fused) return fail(BSGD_ERR_INVALID_ARG, "serving needs one column block per iteration");
+    if (!s->fused && (s->kN > kMaxFusedCols || s->p.pair_sampling != BSGD_PAIRS_UNIFORM))
+        return fail(BSGD_ERR_INVALID_ARG, "serving takes at most 4 column blocks per iteration");
     if (s->p.tv_lambda > 0) return fail(BSGD_ERR_INVALID_ARG, "serving runs no TV prox");
     const bsgd_geometry *g = s->g;
     ReqDesc d{};
@@ -1329,9 +1332,14 @@ bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out) {
     d.x = x;
     d.xlo = s->xlo;
     d.dtype = s->st;
-    d.max_tiles = std::max(1, s->max_tiles);
+    // one block per iteration: items are (tile of the pair's band, view, pair);
+    // several: (tile of the whole-volume band, view, drawn row block), as in
+    // the multi-block fused pass
+    d.kN = s->fused ? 1 : s->kN;
+    const int tiles = s->fused ? s->max_tiles : s->max_tiles_all;
+    d.max_tiles = std::max(1, tiles);
     d.active = s->max_tiles > 0 ? 1 : 0;
-    d.work_count = s->max_tiles > 0 ? (int64_t)s->max_tiles * g->max_views * s->P : 0;
+    d.work_count = s->max_tiles > 0 ? (int64_t)tiles * g->max_views * (s->fused ? s->P : s->kM) : 0;
     int64_t maxJ = 0;
     for (int j = 0; j < g->N; ++j) maxJ = std::max(maxJ, g->block_cols(j));
     d.max_block_cols = maxJ;

@@ -150,3 +150,40 @@ def test_bounded_wait_times_out_and_request_finishes():
         assert rep["iteration"] == 6 * 16 and np.isfinite(x).all() and np.abs(x).max() > 0
     finally:
         srv.close()
+
+
+@pytest.mark.gpu
+def test_several_column_blocks_per_iteration_served():
+    """Requests drawing 2 or 4 column blocks per iteration (the paper's Sec. 5
+    and Sec. 6 settings, here with and without detector cells) served among a
+    one-block request: each equals the plain solver's result. More than 4
+    blocks, or residual pairs with several blocks, are rejected at submit."""
+    geo = cone(64, 96)
+    y, gg = _data(geo, 9)
+    y1, _ = _data(cone(48, 72), 10)
+    p2 = B.SolveParams(alpha=1 / 4, gamma=2 / 4, epochs=3, rho=0.25, power_iters=10,
+                       pair_sampling=B.PAIRS_UNIFORM, seed=11)
+    p4 = B.SolveParams(alpha=1 / 4, gamma=4 / 4, epochs=2, rho=0.25, power_iters=10,
+                       pair_sampling=B.PAIRS_UNIFORM, cells=B.CELLS_GEOMETRIC, n_cells=4,
+                       storage=B.BF16, seed=12)
+    srv = B.Server(budget_bytes=8 << 30, max_slots=8)
+    try:
+        ids = [srv.submit(geo, 4, 4, p2, y), srv.submit(cone(48, 72), 4, 4, params(seed=13), y1),
+               srv.submit(geo, 4, 4, p4, y)]
+        outs = [srv.wait(i) for i in ids]
+        with pytest.raises(B.BSGDError) as ei:
+            srv.submit(geo, 4, 8, B.SolveParams(alpha=1 / 4, gamma=5 / 8, pair_sampling=B.PAIRS_UNIFORM), y)
+        assert ei.value.status == 1
+        with pytest.raises(B.BSGDError) as ei:
+            srv.submit(geo, 4, 4, B.SolveParams(alpha=1 / 4, gamma=2 / 4, pair_sampling=B.PAIRS_RESIDUAL), y)
+        assert ei.value.status == 1
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert st["completed"] == 3 and st["failed"] == 0
+    assert outs[0][1]["iteration"] == 3 * 8 and outs[2][1]["iteration"] == 2 * 4
+    for (x_srv, rep), prm in ((outs[0], p2), (outs[2], p4)):
+        x_plain = np.zeros(gg.n_cols, dtype=np.float32)
+        rp = B.bsgd_solve(gg, prm, y, x_plain)
+        assert rep["updates"] == rp["updates"]
+        assert _rel(x_srv, x_plain) <= (2e-3 if prm.storage == B.BF16 else 1e-5)
