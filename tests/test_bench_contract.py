@@ -1,9 +1,12 @@
-"""The reference arm of bench.py (the FP64 oracle on the host cores) prints one
-JSON line with the keys the measurement contract names. CPU only."""
+"""bench.py prints one JSON line with the keys the measurement contract names:
+the reference arm (the FP64 oracle on the host cores, CPU) and a short run of
+the CUDA arm (GPU)."""
 import json
 import os
 import subprocess
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -25,8 +28,6 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
 
-
-import pytest  # noqa: E402
 
 
 @pytest.mark.gpu
