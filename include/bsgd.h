@@ -68,6 +68,8 @@ typedef enum {
  *    -(dsd - dso)(cos b, sin b, 0), axes u = (-sin b, cos b, 0), v = (0, 0, 1);
  *    one ray from the source to each pixel centre;
  *  - angles == NULL means a * pi / n_views (PAR2D) or a * 2 pi / n_views;
+ *    an angle within 1e-9 rad of a multiple of pi / 2 is taken as that
+ *    multiple exactly (axis-aligned directions);
  *  - a ray lying exactly in a voxel face belongs to the voxel on the + side.
  */
 typedef struct {
