@@ -136,6 +136,10 @@ bsgd_status bsgd_geometry_pair_rays(const bsgd_geometry *g, int i, int j, int64_
  *  row_blocks / col_blocks: host arrays of block ids (n_rb / n_cb entries), or
  *     NULL to select every block. Ids must be distinct and in range.
  * Deterministic: each ray sums its segments in traversal order.
+ * For volumes, the views whose rays run mostly along x gather from a y-fastest
+ * copy of x that the call takes from the library's stream-ordered memory pool
+ * (n_cols elements of type xt, returned when the call's work is done); if the
+ * pool has no room the call reads x directly (same result, slower).
  * Errors: INVALID_ARG, CUDA (launch failure).
  */
 bsgd_status bsgd_forward_project(const bsgd_geometry *g, const void *x, bsgd_dtype xt,
@@ -153,7 +157,10 @@ bsgd_status bsgd_forward_project(const bsgd_geometry *g, const void *x, bsgd_dty
  *     with float atomics). With accumulate = 0 the voxels of the selected
  *     column blocks are cleared first; other voxels are untouched.
  * Not bit-reproducible run to run (atomic order); results agree to float
- * rounding.
+ * rounding. For volumes, the views whose rays run mostly along x scatter into a
+ * y-fastest float32 accumulator from the library's memory pool (n_cols floats),
+ * added into x after each run of column blocks (x directly if the pool has no
+ * room).
  */
 bsgd_status bsgd_back_project(const bsgd_geometry *g, const void *r, bsgd_dtype rt,
                               void *x, bsgd_dtype xt,
@@ -211,8 +218,9 @@ bsgd_status bsgd_power_iteration(const bsgd_geometry *g, int col_block, int iter
  * isotropic TV from backward differences (a missing neighbour gives 0), solved
  * by `iters` FGP iterations (Beck and Teboulle 2009) in FP32.
  *  x: device, n_cols elements of type xt, updated in place.
- * The library allocates (and frees before returning) the dual field
- * (ndim * n_cols floats).
+ * The library allocates (and frees before returning) its workspace: the image
+ * and the primal iterate in FP32 and the dual field and its extrapolation as
+ * four floats per voxel (10 * n_cols floats). Synchronises `stream`.
  */
 bsgd_status bsgd_tv_prox(const bsgd_geometry *g, void *x, bsgd_dtype xt,
                          double kappa, int iters, void *stream);
