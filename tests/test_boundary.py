@@ -66,3 +66,10 @@ def test_null_handles_rejected():
     assert lib.bsgd_geometry_destroy(None) == 1
     assert lib.bsgd_state_destroy(None) == 1
     assert lib.bsgd_block_step(None, None, 1, None) == 1
+    n = ctypes.c_int64(0)
+    assert lib.bsgd_state_checkpoint_bytes(None, ctypes.byref(n)) == 1
+    assert lib.bsgd_state_save(None, None, 0, None) == 1
+    assert lib.bsgd_state_restore(None, None, 0, None) == 1
+    assert lib.bsgd_state_set_split(None, 1) == 1
+    assert lib.bsgd_state_set_sampling(None, 0, 0, 1, None) == 1
+    assert "NULL" in B.load().bsgd_last_error().decode()
