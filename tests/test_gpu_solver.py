@@ -212,6 +212,29 @@ def test_power_iteration_matches_oracle():
     assert abs(st.query()["mu"] - problem("cone_small")[4]) <= 1e-5 * problem("cone_small")[4]
 
 
+def test_block_step_rule_matches_oracle():
+    """BSGD_STEP_BLOCK: mu = rho / max over (row block, column block) of the
+    power-iteration estimate of ||A_(I_i)^(J_j)||^2, against the oracle's power
+    iteration restricted to each row block's views; per-pair estimates through
+    bsgd_power_iteration's row-block list as well."""
+    s, og, gg, _, _, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    lam = np.zeros((M, N))
+    for i in range(M):
+        views = OP.row_block_views(og, M, i)
+        for j in range(N):
+            lam[i, j] = OB.power_iteration(og, N, j, 20, views=views)
+            got = B.bsgd_power_iteration(gg, j, 20, row_blocks=[i])
+            assert abs(got - lam[i, j]) <= 1e-5 * lam[i, j]
+    prm = B.SolveParams(alpha=0.25, gamma=0.25, step_rule=B.STEP_BLOCK, rho=RHO, power_iters=20)
+    st = B.State(gg, prm, torch.zeros(gg.n_rows, device=DEV))
+    mu = RHO / lam.max()
+    assert abs(st.query()["mu"] - mu) <= 1e-5 * mu
+    # a row block sees part of the strip: its norm is below the strip's
+    strip = max(OB.power_iteration(og, N, j, 20) for j in range(N))
+    assert lam.max() < strip
+
+
 @pytest.mark.parametrize("name", ["config1", "cone_small"])
 def test_tv_prox_matches_oracle(name):
     s, og, gg, _, _, xt = problem(name)
