@@ -212,6 +212,32 @@ def test_power_iteration_matches_oracle():
     assert abs(st.query()["mu"] - problem("cone_small")[4]) <= 1e-5 * problem("cone_small")[4]
 
 
+def test_device_replay_of_a_recorded_trace():
+    """bsgd_state_set_replay: a second state consuming the first one's trace
+    (residual pairs with geometric cells, then two column blocks per iteration)
+    takes the same blocks and cells and gives the same image; iterations after
+    the replayed ones sample again."""
+    s, og, gg, y, mu, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    for prm in (B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu, seed=14,
+                              pair_sampling=B.PAIRS_RESIDUAL, cells=B.CELLS_GEOMETRIC, n_cells=4),
+                B.SolveParams(alpha=1 / M, gamma=2 / N, step_rule=B.STEP_FIXED, mu=mu, seed=15)):
+        a, xa = gpu_run(gg, y, prm, 30)
+        ta = a.read_trace(30)
+        other = B.SolveParams(**{**prm.__dict__, "seed": prm.seed + 100})
+        b = B.State(gg, other, torch.from_numpy(y.astype(np.float32)).to(DEV))
+        b.set_replay(ta[:20])
+        xb = torch.zeros(gg.n_cols, device=DEV)
+        b.block_step(xb, 20)
+        torch.cuda.synchronize()
+        assert np.array_equal(b.read_trace(20), ta[:20])
+        xa20 = gpu_run(gg, y, prm, 20)[1]
+        assert rel_l2(xb.cpu().double().numpy(), xa20.cpu().double().numpy()) <= 1e-6
+        b.block_step(xb, 10)       # past the replayed part: b's own seed draws
+        torch.cuda.synchronize()
+        assert not np.array_equal(b.read_trace(30)[20:], ta[20:])
+
+
 def test_block_step_rule_matches_oracle():
     """BSGD_STEP_BLOCK: mu = rho / max over (row block, column block) of the
     power-iteration estimate of ||A_(I_i)^(J_j)||^2, against the oracle's power
