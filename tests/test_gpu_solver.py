@@ -284,6 +284,21 @@ def test_bsgd_tv_matches_oracle():
     assert rel_l2(x.cpu().double().numpy(), ost.x) <= 1e-5
 
 
+@pytest.mark.parametrize("storage", [B.F32, B.BF16])
+def test_bsgd_tv_volume_matches_oracle(storage):
+    """Algorithm 4 on a volume (3D TV), with FP32 storage and with BF16
+    storage, where the prox reads and writes the image with its low-order
+    term: within 1e-5 (FP32) and 1e-2 (BF16) of the FP64 oracle."""
+    s, og, gg, y, mu, _ = problem("cone_small")
+    M, N = s["M"], s["N"]
+    tdt = torch.bfloat16 if storage == B.BF16 else torch.float32
+    prm = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu, seed=3,
+                        tv_lambda=0.5, tv_iters=10, storage=storage)
+    _, x = gpu_run(gg, y, prm, 48, storage=tdt)
+    ost = OB.bsgd(og, y, OB.Params(M, N, 1 / M, 1 / N, mu, seed=3, tv_lambda=0.5, tv_iters=10), 48)
+    assert rel_l2(x.float().cpu().double().numpy(), ost.x) <= (1e-5 if storage == B.F32 else 1e-2)
+
+
 @pytest.mark.parametrize("storage", [B.BF16, B.F16])
 def test_reduced_precision_storage(storage):
     """Sinogram, image and solver state stored in BF16 / FP16 with FP32 ray sums
