@@ -215,6 +215,9 @@ bsgd_status bsgd_power_iteration(const bsgd_geometry *g, int col_block, int iter
 /*
  * TV proximal step of BSGD-TV (Algorithm 4, Eqs. 9-10):
  *   x <- argmin_t ||t - x||^2 + 2 kappa TV(t),   kappa = mu * lambda,
+ * with mu in this library's convention (gradient A^T r, twice the paper's mu):
+ * the weight 2 mu lambda is ISTA's proximal step for the objective of
+ * Eq. (TVequ), 4 mu lambda in the paper's mu (Algorithm 4 prints half that),
  * isotropic TV from backward differences (a missing neighbour gives 0), solved
  * by `iters` FGP iterations (Beck and Teboulle 2009) in FP32.
  *  x: device, n_cols elements of type xt, updated in place.
@@ -255,7 +258,8 @@ typedef struct {
     int pair_sampling;       /* bsgd_pair_sampling                                  */
     int cells;               /* bsgd_cell_sampling                                  */
     int n_cells;             /* 2 (2D: detector halves) or 4 (3D: quadrants)        */
-    double tv_lambda;        /* > 0: BSGD-TV prox every epoch (Algorithm 4)          */
+    double tv_lambda;        /* > 0: BSGD-TV prox every epoch (Algorithm 4), with   */
+                             /* kappa = mu * tv_lambda (see bsgd_tv_prox)           */
     int tv_iters;            /* FGP iterations of the prox                          */
     int storage;             /* bsgd_dtype of y, x, z^j, r and snapshots             */
     uint64_t seed;           /* sampling stream (SplitMix64 counter spec)            */

@@ -1,13 +1,22 @@
 """TV proximal step of BSGD-TV in FP64 -- TEST INFRASTRUCTURE ONLY.
 
-Algorithm 4 replaces x, once every 1/(alpha*gamma) iterations, by
-    argmin_t ||t - x||^2 + 2 mu lambda TV(t)          (Algorithm 4, Eq. 9)
-with the isotropic TV of Eq. 10, built from backward differences
-x[c] - x[c - e_k]. The paper does not say how the minimiser is found; the
-oracle uses FGP (Beck and Teboulle 2009, the FISTA paper the text cites), whose
-problem statement min ||t - b||^2 + 2 kappa TV(t) is exactly this one with
-kappa = mu * lambda. Readings: a difference with a missing neighbour (index 0
-along that axis) is zero; 3D volumes use sqrt(dx^2 + dy^2 + dz^2); no
+Algorithm 4 replaces x, once every 1/(alpha*gamma) iterations, by a TV
+de-noising step argmin_t ||t - x||^2 + w TV(t), with the isotropic TV of
+Eq. 10, built from backward differences x[c] - x[c - e_k].
+
+The weight w: Algorithm 4 prints 2 mu lambda, with mu the step of a gradient
+2 A^T r. The oracle folds that factor 2 into its step (its gradient is A^T r,
+so its mu is twice the paper's) and uses w = 2 mu lambda in its own mu, which
+is 4 mu lambda in the paper's: the weight of ISTA's proximal step for the
+paper's objective, Eq. (TVequ), ||y - A x||^2 + 2 lambda TV(x) (equivalently
+1/2 ||y - A x||^2 + lambda TV(x) with step mu). The printed weight is half of
+that; the objective decides.
+
+The paper does not say how the minimiser is found; the oracle uses FGP (Beck
+and Teboulle 2009, the FISTA paper the text cites), whose problem statement
+min ||t - b||^2 + 2 kappa TV(t) is this one with kappa = mu * lambda (mu in
+the oracle's convention). Readings: a difference with a missing neighbour
+(index 0 along that axis) is zero; 3D volumes use sqrt(dx^2 + dy^2 + dz^2); no
 non-negativity constraint.
 """
 import numpy as np
