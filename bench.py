@@ -320,7 +320,7 @@ def run_cuda(args):
         yh = torch.from_numpy(y_np).pin_memory()
         xh = torch.zeros(gg.n_cols, dtype=torch.float32).pin_memory()
         pe = B.SolveParams(alpha=1 / M, gamma=1 / N, epochs=1, step_rule=B.STEP_FIXED, mu=mu,
-                           pair_sampling=B.PAIRS_RESIDUAL, seed=1 + rank)
+                           pair_sampling=B.PAIRS_RESIDUAL, seed=1 + rank, zero_start=True)
         B.bsgd_solve(gg, pe, yh, xh)       # warm-up
         if world > 1:
             dist.barrier()
@@ -333,7 +333,7 @@ def run_cuda(args):
         t_e2e, upd_e2e = reduce_over_ranks(torch, dist, t_e2e, upd_e2e, dev)
         e2e = {"value": round(upd_e2e / t_e2e / 1e9, 3), "unit": UNIT,
                "h2d_bytes_per_step": int(gg.n_rows * 4), "d2h_bytes_per_step": int(gg.n_cols * 4),
-               "api": "bsgd_solve (1 epoch per call, pinned host y and x, fixed mu)"}
+               "api": "bsgd_solve (1 epoch per call from x0 = 0 (zero_start), pinned host y and x, fixed mu)"}
 
     extra = None
     if not args.no_extra and rank == 0 and world == 1:

@@ -283,6 +283,9 @@ typedef struct {
      * sampling (uniform pairs, whole views), as suggested after Algorithm 2 to
      * remove the sampling's bias from the last iterations (0: off). */
     int final_uniform_epochs;
+    /* bsgd_solve: 1 = start from x0 = 0 (Algorithm 1's start) whatever x holds
+     * on entry, so x is not read (x is then output only); 0 = x holds x0. */
+    int zero_start;
 } bsgd_solve_params;
 
 typedef struct {
@@ -300,9 +303,10 @@ typedef struct {
  * all; a row outside block j's band has z^j = 0), r, the aggregated gradient g
  * (FP32), FP64 residual-norm
  * tables and the sampler's work list, all in library-owned device memory.
- * Initial state is Algorithm 1's: g = 0, z = 0, r = y; x starts at 0 (the caller
- * passes x, zeroed, to bsgd_block_step). Computes mu by power iteration for the
- * STRIP / BLOCK rules. Synchronous.
+ * Initial state is Algorithm 1's: g = 0, z = 0, r = y, for the starting image
+ * x0 = 0; the first bsgd_block_step takes the x it is given as x0 and, when
+ * x0 is not zero, sets z^j = A^j x0_J and r = y - sum_j z^j first (see there).
+ * Computes mu by power iteration for the STRIP / BLOCK rules. Synchronous.
  * Memory: the state's arrays come from a stream-ordered pool per device, owned
  * by the library, that keeps up to 32 GiB of freed memory for reuse by later
  * states (so a state per call costs no page mapping once the pool is warm); the
@@ -325,6 +329,12 @@ bsgd_status bsgd_state_destroy(bsgd_state *s);
  *     With BF16 / FP16 storage the state also keeps the low-order part of x
  *     (compensated storage, so that steps below half an ulp of x accumulate);
  *     change x only through this call while the state lives.
+ * Starting image: the first call on a state (iteration 0, n_iters > 0) takes x
+ * as the starting image x0. Algorithm 1 starts from x0 = 0 with z = 0, r = y;
+ * for x0 != 0 the call first sets z^j = A^j x0_J for every column block (one
+ * FP of x0 over every view), r = y - sum_j z^j, and the residual-norm tables
+ * from that r, with r~^j = 0 and g = 0, so that the memories describe x0. A
+ * zero x0 is detected on the device and costs one read of x.
  * Asynchronous; no host synchronisation inside.
  */
 bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void *stream);
@@ -417,8 +427,10 @@ bsgd_status bsgd_state_restore(bsgd_state *s, const void *host, int64_t bytes, v
 /*
  * One-call reconstruction: state_create, epochs * 1/(alpha*gamma) iterations,
  * query, destroy. y and x may be host or device pointers (host buffers are
- * copied in and out inside the call). x holds x0 = 0 on entry and the
- * reconstruction on return. Synchronous.
+ * copied in and out inside the call). x holds the starting image x0 (type xt;
+ * zero for Algorithm 1's own start) on entry, unless p->zero_start = 1 (then
+ * x0 = 0 and x is not read), and the reconstruction on return; see
+ * bsgd_block_step for the start from x0 != 0. Synchronous.
  */
 bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_params *p,
                        const void *y, bsgd_dtype yt, void *x, bsgd_dtype xt,
@@ -483,8 +495,24 @@ bsgd_status bsgd_server_destroy(bsgd_server *s);
 bsgd_status bsgd_server_submit(bsgd_server *s, const bsgd_geometry_desc *desc, int M, int N,
                                const bsgd_solve_params *p, const void *y, bsgd_dtype yt,
                                float *x_out, int64_t *id);
-/* Wait up to timeout_ms for request id; TIMEOUT if it is still running. */
+/*
+ * Wait up to timeout_ms for request id; TIMEOUT if it is still running. The
+ * report carries the iterations, the update count, the step mu the request
+ * ran with and its residual norm ||y - sum_j z^j|| at the end (FP64).
+ */
 bsgd_status bsgd_server_wait(bsgd_server *s, int64_t id, int timeout_ms, bsgd_report *out);
+/*
+ * Sampling trace of a finished request: the pairs and cells its rounds drew
+ * (Algorithm 1's selection step), in the layout of bsgd_state_read_trace with
+ * *stride int32 entries per iteration (the first 65536 iterations are kept).
+ * With host == NULL only *stride and *n_iters are set; otherwise copies
+ * min(n_iters, cap / stride) iterations to host memory and sets *n_iters to
+ * that. Lets a caller replay a served request elsewhere (an oracle, a plain
+ * state through bsgd_state_set_replay). Errors: INVALID_ARG (unknown id),
+ * STATE (the request has not finished, or failed).
+ */
+bsgd_status bsgd_server_read_trace(bsgd_server *s, int64_t id, int32_t *host, int64_t cap,
+                                   int64_t *stride, int64_t *n_iters);
 /* *done = 1 if request id finished (successfully or not). */
 bsgd_status bsgd_server_poll(bsgd_server *s, int64_t id, int *done);
 bsgd_status bsgd_server_get_stats(bsgd_server *s, bsgd_server_stats *out);

@@ -30,7 +30,7 @@ EXPORTS = (
     "bsgd_state_set_split", "bsgd_state_set_sampling", "bsgd_state_checkpoint_bytes",
     "bsgd_state_save", "bsgd_state_restore", "bsgd_solve",
     "bsgd_request_bytes", "bsgd_server_create", "bsgd_server_destroy", "bsgd_server_submit",
-    "bsgd_server_wait", "bsgd_server_poll", "bsgd_server_get_stats",
+    "bsgd_server_wait", "bsgd_server_read_trace", "bsgd_server_poll", "bsgd_server_get_stats",
 )
 STAGES = ("sample", "fp", "residual", "bp", "update", "tv", "fpbp")
 
@@ -77,7 +77,7 @@ class SolveParamsC(ctypes.Structure):
         ("storage", ctypes.c_int), ("seed", ctypes.c_uint64),
         ("auto_mu", ctypes.c_int), ("auto_window", ctypes.c_int), ("auto_eps", ctypes.c_double),
         ("auto_delta", ctypes.c_double), ("auto_t1", ctypes.c_double), ("auto_t2", ctypes.c_double),
-        ("final_uniform_epochs", ctypes.c_int),
+        ("final_uniform_epochs", ctypes.c_int), ("zero_start", ctypes.c_int),
     ]
 
 
@@ -173,6 +173,8 @@ def load(build_if_missing: bool = True):
                                     P(SolveParamsC), _vp, st, ctypes.POINTER(ctypes.c_float),
                                     P(ctypes.c_int64)]),
         "bsgd_server_wait": (st, [_vp, ctypes.c_int64, ctypes.c_int, P(Report)]),
+        "bsgd_server_read_trace": (st, [_vp, ctypes.c_int64, _i32p, ctypes.c_int64,
+                                        P(ctypes.c_int64), P(ctypes.c_int64)]),
         "bsgd_server_poll": (st, [_vp, ctypes.c_int64, P(ctypes.c_int)]),
         "bsgd_server_get_stats": (st, [_vp, P(ServerStats)]),
     }
@@ -391,6 +393,8 @@ class SolveParams:
     auto_t2: float = 0.5
     # bsgd_solve: last epochs without importance sampling (after Algorithm 2)
     final_uniform_epochs: int = 0
+    # bsgd_solve: start from x0 = 0 without reading x (otherwise x holds x0)
+    zero_start: bool = False
 
     def c(self):
         return SolveParamsC(self.alpha, self.gamma, self.epochs, self.step_rule, self.mu, self.rho,
@@ -398,7 +402,7 @@ class SolveParams:
                             self.tv_lambda, self.tv_iters, self.storage, self.seed,
                             int(bool(self.auto_mu)), self.auto_window, self.auto_eps,
                             self.auto_delta, self.auto_t1, self.auto_t2,
-                            int(self.final_uniform_epochs))
+                            int(self.final_uniform_epochs), int(bool(self.zero_start)))
 
 
 class State:
@@ -566,6 +570,18 @@ class Server:
         _check(load().bsgd_server_wait(self.handle, int(rid), int(timeout_ms), ctypes.byref(rep)))
         x, _keep = self._pending[rid]
         return x, rep.as_dict()
+
+    def read_trace(self, rid: int) -> np.ndarray:
+        """Draws of finished request rid: an (iterations, stride) int32 array in
+        the layout of State.read_trace."""
+        stride, n = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().bsgd_server_read_trace(self.handle, int(rid), None, 0, ctypes.byref(stride),
+                                             ctypes.byref(n)))
+        buf = np.zeros(max(1, n.value * stride.value), dtype=np.int32)
+        _check(load().bsgd_server_read_trace(self.handle, int(rid),
+                                             buf.ctypes.data_as(_i32p), buf.size,
+                                             ctypes.byref(stride), ctypes.byref(n)))
+        return buf[:n.value * stride.value].reshape(n.value, stride.value)
 
     def poll(self, rid: int) -> bool:
         done = ctypes.c_int()

@@ -261,6 +261,11 @@ bsgd_status launch_bp_solve(const bsgd_geometry *g, const SolveDev &S, bsgd_dtyp
 // block paired with every drawn column block: FP, residual and BP in one pass
 // over the bounding box of the selected blocks' bands; grid z = row-block
 // slots (max_rows), max_tiles bounds the tiles of any such box.
+// Algorithm 1 from a starting image x (device, storage type): z^j = A^j x_J in
+// every block's band rows and r = y - sum_j z^j; skipped on the device when x
+// is zero (flag: one device int of scratch).
+bsgd_status launch_warm_start(const bsgd_geometry *g, const SolveDev &S, const void *x,
+                              bsgd_dtype st_t, int *flag, cudaStream_t st);
 constexpr int kMaxFusedCols = 4;
 bsgd_status launch_fpbpm_solve(const bsgd_geometry *g, const SolveDev &S, const void *x,
                                bsgd_dtype st_t, int max_rows, int max_tiles, int n_cols,

@@ -18,6 +18,7 @@
 // when requests join or leave.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -62,6 +63,11 @@ struct Request {
     float *stage = nullptr;       // pinned host staging of the result (+ update count)
     size_t stage_bytes = 0;
     unsigned long long *upd_host = nullptr;  // inside stage
+    // inside stage too: the step, the residual-norm table and the sampling
+    // trace, copied out with the image
+    size_t off_mu = 0, off_S = 0, off_trace = 0;
+    int64_t n_S = 0, trace_rows = 0, stride = 0;
+    std::vector<int32_t> trace;   // the draws, kept after the request retires
     cudaEvent_t ev = nullptr;
     double t_submit = 0, t_done = 0;
     bsgd_report rep{};
@@ -281,7 +287,17 @@ bsgd_status admit_one(bsgd_server *S, Request *r, cudaStream_t stream) {
     BSGD_TRY(pool_alloc(&r->x, C * es, stream));
     BSGD_TRY(pool_alloc((void **)&r->xf, C * 4, stream));
     BSGD_CUDA(cudaMemsetAsync(r->x, 0, C * es, stream));
-    r->stage_bytes = (size_t)C * 4 + 64;
+    {
+        ReqDesc d;
+        BSGD_TRY(state_descriptor(r->st, r->x, &d));
+        r->n_S = (int64_t)r->g->M * r->g->desc.nv;
+        r->stride = d.A.stride;
+        r->trace_rows = std::min<int64_t>(r->target, d.A.trace_cap);
+    }
+    r->off_mu = (size_t)C * 4 + 64;
+    r->off_S = r->off_mu + 8;
+    r->off_trace = r->off_S + 8 * (size_t)r->n_S;
+    r->stage_bytes = r->off_trace + 4 * (size_t)r->trace_rows * r->stride;
     r->stage = take_pinned(S, r->stage_bytes);
     if (!r->stage) return fail(BSGD_ERR_OOM, "pinned staging buffer");
     r->upd_host = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(r->stage) + (size_t)C * 4 + 32);
@@ -382,6 +398,13 @@ bsgd_status start_finish(bsgd_server *S, Request *r) {
     ReqDesc d;
     BSGD_TRY(state_descriptor(r->st, r->x, &d));
     BSGD_CUDA(cudaMemcpyAsync(r->upd_host, d.A.updates, 8, cudaMemcpyDeviceToHost, S->round_stream));
+    char *base = reinterpret_cast<char *>(r->stage);
+    BSGD_CUDA(cudaMemcpyAsync(base + r->off_mu, d.S.mu, 8, cudaMemcpyDeviceToHost, S->round_stream));
+    BSGD_CUDA(cudaMemcpyAsync(base + r->off_S, d.S.S, 8 * (size_t)r->n_S, cudaMemcpyDeviceToHost,
+                              S->round_stream));
+    if (r->trace_rows > 0)
+        BSGD_CUDA(cudaMemcpyAsync(base + r->off_trace, d.A.trace, 4 * (size_t)r->trace_rows * r->stride,
+                                  cudaMemcpyDeviceToHost, S->round_stream));
     BSGD_CUDA(cudaEventRecord(r->ev, S->round_stream));
     return BSGD_OK;
 }
@@ -461,11 +484,24 @@ void round_loop(bsgd_server *S) {
             const int64_t C = r->g->n_cols();
             std::memcpy(r->x_out, r->stage, C * 4);
             const unsigned long long upd = *r->upd_host;
+            const char *base = reinterpret_cast<const char *>(r->stage);
+            double mu = 0.0, rr = 0.0;
+            std::memcpy(&mu, base + r->off_mu, 8);
+            for (int64_t k = 0; k < r->n_S; ++k) {
+                double v;
+                std::memcpy(&v, base + r->off_S + 8 * k, 8);
+                rr += v;
+            }
+            r->trace.resize((size_t)r->trace_rows * r->stride);
+            if (!r->trace.empty()) std::memcpy(r->trace.data(), base + r->off_trace, 4 * r->trace.size());
             free_request_gpu(S, r, S->round_stream);
             std::lock_guard<std::mutex> lk(S->mu);
             r->t_done = now_s();
             r->rep.iteration = r->target;
             r->rep.updates = (int64_t)upd;
+            r->rep.mu = mu;
+            r->rep.residual_norm = std::sqrt(std::max(rr, 0.0));
+            r->rep.epoch = (double)r->p.epochs;
             r->status = kDone;
             S->completed++;
             S->updates += (int64_t)upd;
@@ -654,6 +690,24 @@ extern "C" bsgd_status bsgd_server_wait(bsgd_server *S, int64_t id, int timeout_
     if (!fin) return fail(BSGD_ERR_TIMEOUT, "request " + std::to_string(id) + " still running");
     if (r->status == kFailed) return fail(BSGD_ERR_CUDA, "request failed: " + r->error);
     if (out) *out = r->rep;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_server_read_trace(bsgd_server *S, int64_t id, int32_t *host, int64_t cap,
+                                              int64_t *stride, int64_t *n_iters) {
+    if (!S || !stride || !n_iters) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return fail(BSGD_ERR_INVALID_ARG, "unknown request id");
+    const Request *r = it->second;
+    if (r->status != kDone) return fail(BSGD_ERR_STATE, "request has not finished");
+    *stride = r->stride;
+    *n_iters = r->stride > 0 ? (int64_t)r->trace.size() / r->stride : 0;
+    if (!host) return BSGD_OK;
+    if (cap < 0) return fail(BSGD_ERR_INVALID_ARG, "cap < 0");
+    const int64_t n = std::min(*n_iters, r->stride > 0 ? cap / r->stride : 0);
+    std::memcpy(host, r->trace.data(), 4 * (size_t)n * r->stride);
+    *n_iters = n;
     return BSGD_OK;
 }
 

@@ -473,6 +473,71 @@ __global__ void __launch_bounds__(128) bp_solve_kernel(const DeviceGeom G, const
 }
 
 // ---------------------------------------------------------------------------
+// Warm start (a starting image x0 != 0): z^j = A^j x0_J for every row of every
+// block's band, then r = y - sum_j z^j. Every kernel returns at once when the
+// flag says x0 is zero, so Algorithm 1's own start costs one read of the image.
+
+template <typename T>
+__global__ void __launch_bounds__(256) nonzero_kernel(const T *__restrict__ x, int64_t n,
+                                                      int *__restrict__ flag) {
+    bool nz = false;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        nz |= ldf(x + k) != 0.f;
+    if (__syncthreads_or(nz) && threadIdx.x == 0) *flag = 1;
+}
+
+// z^j of block j at every view: grid x = tile of the view's band, y = views
+// (strided when there are more than gridDim.y).
+template <bool k3D, typename T>
+__global__ void __launch_bounds__(128) warm_fp_kernel(const DeviceGeom G, int j,
+                                                      const T *__restrict__ x,
+                                                      const T *__restrict__ xT, T *__restrict__ z,
+                                                      const int *__restrict__ flag) {
+    if (*flag == 0) return;
+    for (int a = blockIdx.y; a < G.n_views; a += gridDim.y) {
+        const Band b = G.bands[(size_t)a * (G.N + 1) + j];
+        int u, v, nt;
+        if (!tile_pixel<k3D>(b, blockIdx.x, u, v, nt)) continue;
+        const bool yf = xT != nullptr && G.view_yfast[a];
+        const T *src = yf ? xT : x;
+        RayWalk w;
+        float acc = 0.f;
+        if (ray_setup(G, a, u, v, G.plane_start[j], G.plane_start[j + 1], w, yf)) {
+            ray_walk_fast(w, [&](int idx, float s) { acc = fmaf(s, ldf(src + idx), acc); });
+            acc *= w.L;
+        }
+        bool in;
+        stf(z + zslot(G, j, a, u, v, in), acc);
+    }
+}
+
+// r = y - sum_j z^j over every row, the blocks summed in block order as in the
+// solver's FP epilogue (z^j is 0 outside block j's band).
+template <typename T>
+__global__ void __launch_bounds__(256) warm_residual_kernel(const DeviceGeom G,
+                                                            const T *__restrict__ y,
+                                                            const T *__restrict__ z,
+                                                            T *__restrict__ r,
+                                                            const int *__restrict__ flag) {
+    if (*flag == 0) return;
+    const int64_t n = (int64_t)G.n_views * G.nv * G.nu;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        const int u = (int)(row % G.nu);
+        const int64_t av = row / G.nu;
+        const int v = (int)(av % G.nv), a = (int)(av / G.nv);
+        float zs = 0.f;
+        for (int jj = 0; jj < G.N; ++jj) {
+            bool in;
+            const int64_t k = zslot(G, jj, a, u, v, in);
+            if (in) zs += ldf(z + k);
+        }
+        stf(r + row, ldf(y + row) - zs);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Serving rounds: persistent kernels over the work items of every resident
 // request (one CTA work item = one detector tile of one view of one pair).
 // Items are handed out by an atomic counter, so requests of very different
@@ -759,6 +824,38 @@ bsgd_status launch_fpbpm_solve(const bsgd_geometry *g, const SolveDev &S, const 
     else { FPBPM_T(__half) }
 #undef FPBPM_T
 #undef FPBPM_GO
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+bsgd_status launch_warm_start(const bsgd_geometry *g, const SolveDev &S, const void *x,
+                              bsgd_dtype st_t, int *flag, cudaStream_t st) {
+    const int64_t C = g->n_cols(), R = g->n_rows();
+    BSGD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    const int gn = (int)std::max<int64_t>(1, std::min<int64_t>((C + 255) / 256, 152 * 8));
+    const int gr = (int)std::max<int64_t>(1, std::min<int64_t>((R + 255) / 256, 152 * 8));
+    std::vector<int> all(g->desc.n_views);
+    for (int a = 0; a < g->desc.n_views; ++a) all[a] = a;
+    const bool t3 = g->desc.nv > 1;
+#define WARM_GO(T)                                                                                 \
+    {                                                                                              \
+        nonzero_kernel<T><<<gn, 256, 0, st>>>((const T *)x, C, flag);                             \
+        for (int j = 0; j < g->N; ++j) {                                                           \
+            const int tiles = tiles_for(g, all, j, j + 1, tile_u(g), tile_v(g));                   \
+            if (tiles == 0) continue;                                                              \
+            dim3 grid(tiles, std::min(g->desc.n_views, 65535));                                    \
+            if (t3) warm_fp_kernel<true, T><<<grid, 128, 0, st>>>(g->dg, j, (const T *)x,          \
+                                                                  (const T *)S.xT, (T *)S.z, flag);\
+            else warm_fp_kernel<false, T><<<grid, 128, 0, st>>>(g->dg, j, (const T *)x,            \
+                                                                (const T *)S.xT, (T *)S.z, flag);  \
+        }                                                                                          \
+        warm_residual_kernel<T><<<gr, 256, 0, st>>>(g->dg, (const T *)S.y, (const T *)S.z,         \
+                                                    (T *)S.r, flag);                               \
+    }
+    if (st_t == BSGD_F32) WARM_GO(float)
+    else if (st_t == BSGD_BF16) WARM_GO(__nv_bfloat16)
+    else WARM_GO(__half)
+#undef WARM_GO
     BSGD_CUDA(cudaGetLastError());
     return BSGD_OK;
 }

@@ -752,6 +752,7 @@ struct bsgd_state {
     Work *work = nullptr;
     int *cells = nullptr, *wband = nullptr;
     int64_t *d_iter = nullptr;
+    int *x0_flag = nullptr;     // warm start: 1 if the starting image is not zero
     int32_t *trace = nullptr, *replay = nullptr;
     int64_t replay_start = 0, replay_n = 0;
     unsigned long long *counts = nullptr, *updates = nullptr;
@@ -872,7 +873,7 @@ static void free_state(bsgd_state *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     // counts and cw belong to the geometry's cache; replay is a plain allocation
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->trace, s->updates, s->pair_upd, s->eud,
+                    s->wband, s->d_iter, s->x0_flag, s->trace, s->updates, s->pair_upd, s->eud,
                     s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) pfree(p);
     cudaFree(s->replay);
@@ -1152,7 +1153,7 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         (e = palloc((void **)&s->d_mu, 8, st)) || (e = palloc((void **)&s->work, 2 * sizeof(Work), st)) ||
         (e = palloc((void **)&s->cells, 2 * 4 * (size_t)kMaxPairs * g->max_views, st)) ||
         (e = palloc((void **)&s->wband, 4 * g->wband.size(), st)) ||
-        (e = palloc((void **)&s->d_iter, 8, st)) ||
+        (e = palloc((void **)&s->d_iter, 8, st)) || (e = palloc((void **)&s->x0_flag, 8, st)) ||
         (e = palloc((void **)&s->trace, 4 * (size_t)s->trace_cap * s->stride, st)) ||
         (e = palloc((void **)&s->updates, 8, st)) ||
         (e = palloc((void **)&s->pair_upd, 8 * (size_t)M * N, st)) ||
@@ -1264,7 +1265,7 @@ void state_release(bsgd_state *s, cudaStream_t st) {
     }
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->trace, s->updates, s->pair_upd, s->eud,
+                    s->wband, s->d_iter, s->x0_flag, s->trace, s->updates, s->pair_upd, s->eud,
                     s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) pool_free(p, st);
     delete s;
@@ -1502,11 +1503,28 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st, bool d
     return BSGD_OK;
 }
 
+// The first iteration of a state starts from the caller's image x0 (Algorithm 1
+// starts from x0 = 0, z = 0, r = y): z^j = A^j x0_J for every block, r = y -
+// sum_j z^j, then the residual table (and Algorithm 3's first residual norm)
+// from that r; r~^j and g stay 0. All of it is skipped on the device when x0
+// is zero.
+static bsgd_status warm_start(bsgd_state *s, void *x, cudaStream_t st) {
+    const bsgd_geometry *g = s->g;
+    BSGD_TRY(launch_warm_start(g, s->dev, x, s->st, s->x0_flag, st));
+    BSGD_TRY(norm_table(g, s->r, s->st, s->S, st));
+    if (s->am) {
+        automu_init_kernel<<<1, 256, 0, st>>>(s->S, g->M * g->desc.nv, s->am);
+        BSGD_CUDA(cudaGetLastError());
+    }
+    return BSGD_OK;
+}
+
 extern "C" bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void *stream) {
     if (!s || !x) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
     if (n_iters < 0) return fail(BSGD_ERR_INVALID_ARG, "n_iters < 0");
     cudaStream_t st = (cudaStream_t)stream;
     if (n_iters > 0) BSGD_TRY(sync_xT(s, x, st));
+    if (n_iters > 0 && s->iters == 0) BSGD_TRY(warm_start(s, x, st));
     for (int k = 0; k < n_iters; ++k) BSGD_TRY(one_iteration(s, x, st, k > 0, k + 1 < n_iters));
     return BSGD_OK;
 }
@@ -1799,18 +1817,26 @@ extern "C" bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_param
         BSGD_TRY(bsgd_state_create(g, p, yy, yt, stream, &s));
         const bsgd_dtype sd = (bsgd_dtype)p->storage;
         BSGD_TRY(palloc(&xs, C * dtype_size(sd), st));
-        BSGD_CUDA(cudaMemsetAsync(xs, 0, C * dtype_size(sd), st));
+        // x holds the starting image x0 (the first block step warm-starts from
+        // it) unless the caller asks for Algorithm 1's zero start
+        if (xh) BSGD_TRY(palloc(&dx, C * dtype_size(xt), st));
+        if (p->zero_start) {
+            BSGD_CUDA(cudaMemsetAsync(xs, 0, C * dtype_size(sd), st));
+        } else {
+            const void *x0 = x;
+            if (xh) {
+                BSGD_CUDA(cudaMemcpyAsync(dx, x, C * dtype_size(xt), cudaMemcpyHostToDevice, st));
+                x0 = dx;
+            }
+            BSGD_TRY(convert(x0, xt, xs, sd, C, st));
+        }
         const int fin = std::max(0, std::min(p->final_uniform_epochs, p->epochs));
         BSGD_TRY(bsgd_block_step(s, xs, (p->epochs - fin) * s->epoch_len, stream));
         if (fin > 0) {   // last epochs without importance sampling (after Algorithm 2)
             BSGD_TRY(bsgd_state_set_sampling(s, BSGD_PAIRS_UNIFORM, BSGD_CELLS_NONE, 1, stream));
             BSGD_TRY(bsgd_block_step(s, xs, fin * s->epoch_len, stream));
         }
-        void *xo = x;
-        if (xh) {
-            BSGD_TRY(palloc(&dx, C * dtype_size(xt), st));
-            xo = dx;
-        }
+        void *xo = xh ? dx : x;
         BSGD_TRY(convert(xs, sd, xo, xt, C, st));
         if (xh) BSGD_CUDA(cudaMemcpyAsync(x, dx, C * dtype_size(xt), cudaMemcpyDeviceToHost, st));
         if (out) BSGD_TRY(bsgd_state_query(s, out, stream));

@@ -490,3 +490,65 @@ def test_solve_final_uniform_epochs_equals_manual_switch():
     with pytest.raises(B.BSGDError):
         B.State(gg, B.SolveParams(alpha=2 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu),
                 torch.from_numpy(y.astype(np.float32)).to(DEV)).set_sampling(B.PAIRS_RESIDUAL, B.CELLS_NONE)
+
+
+# --------------------------------------------------------------------------
+# Starting image x0 != 0 (the first block step sets z^j = A^j x0_J and
+# r = y - sum_j z^j before its first iteration)
+
+def warm_x0(og, xt, seed):
+    return (0.5 * xt + 0.05 * synth.normal_array(og.n_cols, seed)).astype(np.float32)
+
+
+def test_warm_start_one_call_solve_matches_oracle():
+    """Config 1 through bsgd_solve with host buffers, x holding x0 on entry:
+    three epochs of uniform draws (the same on both sides) against the oracle
+    started at the same x0."""
+    s, og, gg, y, mu, xt = problem("config1")
+    M, N = s["M"], s["N"]
+    x0 = warm_x0(og, xt, 31)
+    prm = B.SolveParams(alpha=0.25, gamma=0.25, epochs=3, step_rule=B.STEP_FIXED, mu=mu, seed=3)
+    xh = x0.copy()
+    rep = B.bsgd_solve(gg, prm, y.astype(np.float32), xh)
+    ost = OB.bsgd(og, y, OB.Params(M, N, 0.25, 0.25, mu, seed=3), 48, x0=x0.astype(np.float64))
+    assert rep["iteration"] == 48
+    assert rel_l2(xh, ost.x) <= 1e-5
+    assert abs(rep["residual_norm"] - ost.residual_norm()) <= 1e-5 * np.linalg.norm(y)
+    # the start mattered: from zero the same draws end elsewhere
+    assert rel_l2(OB.bsgd(og, y, OB.Params(M, N, 0.25, 0.25, mu, seed=3), 48).x, ost.x) > 1e-3
+
+
+@pytest.mark.parametrize("storage", [torch.float32, torch.bfloat16])
+def test_warm_start_block_steps_match_oracle(storage):
+    """cone_small, residual-weighted pairs with geometric cells: a state whose
+    first block step is given x0; the oracle, started at the same x0 (rounded
+    to the storage type), replays the GPU's draws. FP32 within 1e-5, BF16
+    storage within 1e-2."""
+    s, og, gg, y, mu, xt = problem("cone_small")
+    M, N = s["M"], s["N"]
+    code = B.F32 if storage == torch.float32 else B.BF16
+    prm = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu, seed=17,
+                        pair_sampling=B.PAIRS_RESIDUAL, cells=B.CELLS_GEOMETRIC, n_cells=4,
+                        storage=code)
+    x0 = torch.from_numpy(warm_x0(og, xt, 32)).to(DEV).to(storage)
+    iters = 24
+    st, x = gpu_run(gg, y, prm, iters, x=x0.clone())
+    tr = st.read_trace(iters)
+    po = OB.Params(M, N, 1 / M, 1 / N, mu, seed=17, pair_sampling="residual", cells="geometric",
+                   n_cells=4)
+    sels = oracle_replay(tr, 1, gg.info.max_views_per_block, M, og, po, True)
+    ost = OB.bsgd(og, y, po, iters, x0=x0.float().cpu().double().numpy(), replay=sels)
+    tol = 1e-5 if storage == torch.float32 else 1e-2
+    assert rel_l2(x.float().cpu().numpy(), ost.x) <= tol
+    assert abs(st.query()["residual_norm"] - ost.residual_norm()) <= tol * ost.residual_norm()
+
+
+def test_zero_start_does_not_read_x():
+    """zero_start = 1: bsgd_solve starts from x0 = 0 whatever x holds."""
+    s, og, gg, y, mu, _ = problem("config1")
+    kw = dict(alpha=0.25, gamma=0.25, epochs=2, step_rule=B.STEP_FIXED, mu=mu, seed=4)
+    xa = np.zeros(og.n_cols, dtype=np.float32)
+    B.bsgd_solve(gg, B.SolveParams(**kw), y.astype(np.float32), xa)
+    xb = synth.normal_array(og.n_cols, 33).astype(np.float32)
+    B.bsgd_solve(gg, B.SolveParams(zero_start=True, **kw), y.astype(np.float32), xb)
+    assert rel_l2(xb, xa) <= 1e-6

@@ -263,3 +263,35 @@ def test_bsgd_tv_small_lambda_is_plain_bsgd():
     a = B.bsgd(geom, y, B.Params(2, 2, 0.5, 0.5, mu, seed=6, tv_lambda=1e-12), 12)
     b = B.bsgd(geom, y, B.Params(2, 2, 0.5, 0.5, mu, seed=6), 12)
     np.testing.assert_allclose(a.x, b.x, rtol=0, atol=1e-9 * np.abs(b.x).max())
+
+
+# --------------------------------------------------------------------------
+# Starting image x0 != 0: z^j = A^j x0_J, r = y - sum_j z^j, r~ = 0, g = 0
+
+def test_start_from_x0_all_blocks_is_gradient_descent_from_x0():
+    """M = N = 1: the iterates are gradient descent started at x0."""
+    geom, A, y, _ = paper_2d_problem()
+    mu = 0.9 / np.linalg.norm(A, 2) ** 2
+    x0 = synth.normal_array(A.shape[1], 21)
+    st = B.bsgd(geom, y, B.Params(1, 1, 1.0, 1.0, mu), 25, x0=x0)
+    x = x0.copy()
+    for _ in range(25):
+        x = x + mu * A.T @ (y - A @ x)
+    np.testing.assert_allclose(st.x, x, rtol=0, atol=1e-11 * np.abs(x).max())
+
+
+def test_start_at_the_least_squares_solution_stays_there():
+    """Sec. 4: x_lsq is the fixed point. Started there with every block in
+    every iteration (M = 4, N = 2, alpha = gamma = 1), each iteration's memories
+    sum to g = A^T (y - A x_lsq) = 0, so x does not move; the memories z^j of
+    the start give r = y - A x_lsq."""
+    geom, A, y, x_ls = paper_2d_problem()
+    prm = B.Params(4, 2, 1.0, 1.0, B.step_strip(geom, 2), seed=9)
+    st = B.BSGDState(geom, y, prm, x0=x_ls)
+    np.testing.assert_allclose(st.r, y - A @ x_ls, rtol=0, atol=1e-12 * np.abs(y).max())
+    for j in range(2):
+        vox = P.column_block_voxels(geom, 2, j)
+        np.testing.assert_allclose(st.z[j], A[:, vox] @ x_ls[vox], rtol=0, atol=1e-12 * np.abs(y).max())
+    for _ in range(5):
+        st.step()
+    assert np.linalg.norm(st.x - x_ls) <= 1e-9 * np.linalg.norm(x_ls)

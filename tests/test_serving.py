@@ -99,12 +99,15 @@ def test_results_alone_equal_results_in_the_mix():
             time.sleep(0.001)
         ids = [idb, srv.submit(geoA, 4, 4, pA, yA), srv.submit(geoC, 4, 4, params(B.BF16, seed=7), yC)]
         outs = [srv.wait(i) for i in ids]
+        traces = {1: srv.read_trace(ids[1]), 2: srv.read_trace(ids[2])}
+        trace_alone = srv.read_trace(ida)
         st = srv.stats()
     finally:
         srv.close()
     x_mix = outs[1][0]
     assert _rel(x_mix, x_alone) <= 1e-5
     assert outs[1][1]["iteration"] == rep_alone["iteration"] == 2 * 16
+    assert np.array_equal(traces[1], trace_alone)   # same draws alone and in the mix
     assert st["completed"] == 4 and st["failed"] == 0
     assert st["peak_resident"] >= 2          # the requests overlapped on the GPU
     # the plain one-call solver, same parameters and seed
@@ -112,6 +115,28 @@ def test_results_alone_equal_results_in_the_mix():
     x_plain = np.zeros(ggA.n_cols, dtype=np.float32)
     B.bsgd_solve(ggA, pA, yA, x_plain)
     assert _rel(x_alone, x_plain) <= 1e-5
+    # the served results against the FP64 oracle: Algorithm 1 with the served
+    # request's own draws and step, FP32 request A within 1e-5, BF16-storage
+    # request C within 1e-2
+    for k, geo, yk, seed, tol in ((1, geoA, yA, 5, 1e-5), (2, geoC, yC, 7, 1e-2)):
+        x_srv, rep = outs[k]
+        x_o, rn_o = oracle_replay_served(geo, yk, seed, rep["mu"], traces[k])
+        assert traces[k].shape[0] == rep["iteration"] == 2 * 16
+        assert _rel(x_srv, x_o) <= tol, k
+        assert abs(rep["residual_norm"] - rn_o) <= tol * rn_o, k
+
+
+def oracle_replay_served(geo, y, seed, mu, trace, M=4, N=4):
+    """Run the FP64 oracle on a served request's own draws (one pair per
+    iteration: trace row = [1, i, j, ...]); returns (x, ||y - sum_j z^j||)."""
+    from oracle import bsgd as OB
+    from oracle import projector as OP
+    og = OP.Geometry(**geo)
+    prm = OB.Params(M, N, 1 / M, 1 / N, mu, seed=seed, pair_sampling="residual")
+    sels = [OB.Selection([(int(t[1]), int(t[2]))], [None]) for t in trace]
+    assert all(int(t[0]) == 1 for t in trace)
+    ost = OB.bsgd(og, np.asarray(y, dtype=np.float64), prm, len(sels), replay=sels)
+    return ost.x, ost.residual_norm()
 
 
 @pytest.mark.gpu
