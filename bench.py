@@ -578,6 +578,52 @@ def precision_leg(B, torch, dev, epochs=2):
     d = float(torch.linalg.vector_norm(xs["bf16"] - xs["fp32"]) / torch.linalg.vector_norm(xs["fp32"]))
     out["bf16_vs_fp32_rel_l2"] = round(d, 6)
     out["mu"] = lam
+    out["vs_oracle_reduced"] = precision_vs_oracle(B, torch, dev)
+    return out
+
+
+def precision_vs_oracle(B, torch, dev):
+    """The same BSGD-TV set-up at 1/8 resolution (synth.PRECISION_REDUCED: 64^3,
+    90 views, 64^2 detector, 16 x 16 blocks, 10 epochs) against the FP64
+    oracle's stored trajectory (tests/golden/precision_reduced.json, written by
+    tests/golden/make_precision_reduced.py; same draws and step): relative L2
+    error after every epoch over the stored sample voxels, for FP32 storage,
+    BF16 with the compensated image and BF16 with the plain image."""
+    import numpy as np
+    from paper_1903_11874_gb300 import synth
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                        "precision_reduced.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        gold = json.load(f)
+    w = synth.PRECISION_REDUCED
+    gg = B.Geometry(M=w["M"], N=w["N"], **w["geometry"])
+    vol = torch.from_numpy(synth.precision_reduced_phantom().reshape(-1)).to(dev)
+    y = torch.zeros(gg.n_rows, device=dev)
+    B.bsgd_forward_project(gg, vol, y)
+    idx = torch.tensor(gold["sample_indices"], device=dev)
+    ref = [torch.tensor(v, device=dev, dtype=torch.float64) for v in gold["x_samples"]]
+    out = {"workload": "64^3 (4 mm), 90 views, 64^2 detector (6.4 mm), M=N=16, BSGD-TV lambda 1e-3, "
+                       "10 epochs, noise-free; y by this library's FP (the oracle's own y differs by "
+                       "FP32 rounding)",
+           "samples": len(gold["sample_indices"]), "mu": gold["mu"]}
+    for name, storage, tdt, plain in (("fp32", B.F32, torch.float32, False),
+                                      ("bf16", B.BF16, torch.bfloat16, False),
+                                      ("bf16_plain", B.BF16, torch.bfloat16, True)):
+        prm = B.SolveParams(alpha=1 / w["M"], gamma=1 / w["N"], step_rule=B.STEP_FIXED,
+                            mu=gold["mu"], seed=w["seed"], tv_lambda=w["tv_lambda"],
+                            tv_iters=w["tv_iters"], storage=storage, image_plain=plain)
+        st = B.State(gg, prm, y)
+        x = torch.zeros(gg.n_cols, device=dev, dtype=tdt)
+        errs = []
+        for e in range(w["epochs"]):
+            st.block_step(x, w["M"] * w["N"])
+            got = x.double()[idx]
+            errs.append(float(torch.linalg.vector_norm(got - ref[e]) / torch.linalg.vector_norm(ref[e])))
+        st.close()
+        out[name + "_rel_l2_per_epoch"] = [float("%.3e" % v) for v in errs]
+    out["image_bytes_per_voxel"] = {"fp32": 4, "bf16": 4, "bf16_plain": 2}
     return out
 
 

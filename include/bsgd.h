@@ -286,6 +286,11 @@ typedef struct {
     /* bsgd_solve: 1 = start from x0 = 0 (Algorithm 1's start) whatever x holds
      * on entry, so x is not read (x is then output only); 0 = x holds x0. */
     int zero_start;
+    /* BF16 / FP16 storage: 1 = keep the image in the storage type alone (round
+     * to nearest at every update and after the TV prox: 2 bytes per voxel, but
+     * a step below half an ulp of x is lost); 0 = compensated storage, a
+     * low-order 16-bit term beside x (4 bytes per voxel). Ignored for FP32. */
+    int image_plain;
 } bsgd_solve_params;
 
 typedef struct {
@@ -341,6 +346,49 @@ bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void *stream);
 
 /* Progress of the state. Synchronises `stream`. */
 bsgd_status bsgd_state_query(bsgd_state *s, bsgd_report *out, void *stream);
+
+/*
+ * The state's residual r = y - sum_j z^j (Algorithm 1's r, as the last FP
+ * epilogues left it): n_rows elements, [view][v][u], converted from the
+ * storage type into out (device, n_rows elements of type ot). Asynchronous.
+ */
+bsgd_status bsgd_state_read_residual(bsgd_state *s, void *out, bsgd_dtype ot, void *stream);
+
+/*
+ * Owner-computes sharding across processes (Sec. 2 and Fig. 1: the nodes hold
+ * the column blocks x_J and compute A_I^J x_J; the sums over J that form r_I
+ * are collected in one place). Each process (one per GPU) creates a state of
+ * the whole problem (same geometry, parameters and y) and marks the column
+ * blocks it owns; it then computes the FP, BP and update only for those
+ * blocks, keeping x_J, g_J, z^J and r~^J of its own blocks current, and a
+ * replicated r. One iteration:
+ *   bsgd_shard_begin  draw the pairs (uniform draws, the same on every
+ *                     process), FP of the owned drawn pairs into z^J, and
+ *                     this process's part sum_{J owned} z^J of the rows whose
+ *                     z changed (the bounding box of the drawn blocks' bands
+ *                     in every view of the drawn row blocks) into `exchange`;
+ *   (caller)          sum `exchange` over all processes (one all-reduce of
+ *                     *exchange_len floats, e.g. NCCL or gloo);
+ *   bsgd_shard_end    r = y - (the summed buffer) on those rows, the residual
+ *                     table, BP of r - r~^J into g_J and x_J += mu g_J for the
+ *                     owned drawn blocks.
+ * Blocks that no process owns are never updated; a block owned by two
+ * processes would be counted twice. x: device, the state's storage type,
+ * whole-image layout; only the owned blocks' voxels are read or written, and
+ * every process's x must be zero at the start (x0 = 0). Supported: uniform
+ * pairs, whole views or uniform cells; no TV prox, no automatic step, no
+ * replay (INVALID_ARG); call before the first iteration (STATE otherwise).
+ * The report's update count is the whole iteration's on every process.
+ * bsgd_state_set_shard: owned_blocks host array of n_owned ids; sets
+ *   *exchange_len (floats) for the caller's buffer (device, float32, layout
+ *   [drawn row block][view of the block][v][u]). Synchronous.
+ * bsgd_shard_begin / _end: asynchronous on `stream`; the same `exchange`
+ *   buffer must hold the all-reduced sum when _end is called.
+ */
+bsgd_status bsgd_state_set_shard(bsgd_state *s, const int32_t *owned_blocks, int n_owned,
+                                 int64_t *exchange_len);
+bsgd_status bsgd_shard_begin(bsgd_state *s, void *x, float *exchange, void *stream);
+bsgd_status bsgd_shard_end(bsgd_state *s, void *x, const float *exchange, void *stream);
 
 /*
  * Sampling trace. Each iteration occupies bsgd_trace_stride() int32 entries:

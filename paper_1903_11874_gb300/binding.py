@@ -25,7 +25,8 @@ EXPORTS = (
     "bsgd_last_error", "bsgd_status_string", "bsgd_geometry_create", "bsgd_geometry_destroy",
     "bsgd_geometry_get_info", "bsgd_geometry_pair_rays", "bsgd_forward_project", "bsgd_back_project", "bsgd_count_updates",
     "bsgd_count_updates_noalloc", "bsgd_power_iteration", "bsgd_tv_prox", "bsgd_state_create", "bsgd_state_destroy",
-    "bsgd_block_step", "bsgd_state_query", "bsgd_trace_stride", "bsgd_state_read_trace",
+    "bsgd_block_step", "bsgd_state_query", "bsgd_state_read_residual", "bsgd_trace_stride",
+    "bsgd_state_read_trace", "bsgd_state_set_shard", "bsgd_shard_begin", "bsgd_shard_end",
     "bsgd_state_set_replay", "bsgd_state_profile", "bsgd_state_read_profile",
     "bsgd_state_set_split", "bsgd_state_set_sampling", "bsgd_state_checkpoint_bytes",
     "bsgd_state_save", "bsgd_state_restore", "bsgd_solve",
@@ -78,6 +79,7 @@ class SolveParamsC(ctypes.Structure):
         ("auto_mu", ctypes.c_int), ("auto_window", ctypes.c_int), ("auto_eps", ctypes.c_double),
         ("auto_delta", ctypes.c_double), ("auto_t1", ctypes.c_double), ("auto_t2", ctypes.c_double),
         ("final_uniform_epochs", ctypes.c_int), ("zero_start", ctypes.c_int),
+        ("image_plain", ctypes.c_int),
     ]
 
 
@@ -154,6 +156,10 @@ def load(build_if_missing: bool = True):
         "bsgd_state_destroy": (st, [_vp]),
         "bsgd_block_step": (st, [_vp, _vp, ctypes.c_int, _vp]),
         "bsgd_state_query": (st, [_vp, P(Report), _vp]),
+        "bsgd_state_read_residual": (st, [_vp, _vp, st, _vp]),
+        "bsgd_state_set_shard": (st, [_vp, _i32p, ctypes.c_int, P(ctypes.c_int64)]),
+        "bsgd_shard_begin": (st, [_vp, _vp, _vp, _vp]),
+        "bsgd_shard_end": (st, [_vp, _vp, _vp, _vp]),
         "bsgd_trace_stride": (ctypes.c_int64, [_vp]),
         "bsgd_state_read_trace": (st, [_vp, _i32p, ctypes.c_int64, ctypes.c_int64, _vp]),
         "bsgd_state_set_replay": (st, [_vp, _i32p, ctypes.c_int64]),
@@ -395,6 +401,8 @@ class SolveParams:
     final_uniform_epochs: int = 0
     # bsgd_solve: start from x0 = 0 without reading x (otherwise x holds x0)
     zero_start: bool = False
+    # 16-bit storage: the image without its low-order term (2 B / voxel)
+    image_plain: bool = False
 
     def c(self):
         return SolveParamsC(self.alpha, self.gamma, self.epochs, self.step_rule, self.mu, self.rho,
@@ -402,7 +410,8 @@ class SolveParams:
                             self.tv_lambda, self.tv_iters, self.storage, self.seed,
                             int(bool(self.auto_mu)), self.auto_window, self.auto_eps,
                             self.auto_delta, self.auto_t1, self.auto_t2,
-                            int(self.final_uniform_epochs), int(bool(self.zero_start)))
+                            int(self.final_uniform_epochs), int(bool(self.zero_start)),
+                            int(bool(self.image_plain)))
 
 
 class State:
@@ -424,6 +433,29 @@ class State:
         rep = Report()
         _check(load().bsgd_state_query(self.handle, ctypes.byref(rep), _stream(stream)))
         return rep.as_dict()
+
+    def read_residual(self, out, stream=None):
+        """r = y - sum_j z^j into the device tensor out (n_rows elements)."""
+        _check(load().bsgd_state_read_residual(self.handle, _dev_ptr(out, "out"), dtype_code(out),
+                                               _stream(stream)))
+        return out
+
+    def set_shard(self, owned_blocks) -> int:
+        """Mark the column blocks this process owns (owner-computes sharding);
+        returns the length (floats) of the exchange buffer."""
+        ids = np.ascontiguousarray(np.asarray(list(owned_blocks), dtype=np.int32))
+        n = ctypes.c_int64()
+        _check(load().bsgd_state_set_shard(self.handle, ids.ctypes.data_as(_i32p), int(ids.size),
+                                           ctypes.byref(n)))
+        return int(n.value)
+
+    def shard_begin(self, x, exchange, stream=None):
+        _check(load().bsgd_shard_begin(self.handle, _dev_ptr(x, "x"), _dev_ptr(exchange, "exchange"),
+                                       _stream(stream)))
+
+    def shard_end(self, x, exchange, stream=None):
+        _check(load().bsgd_shard_end(self.handle, _dev_ptr(x, "x"), _dev_ptr(exchange, "exchange"),
+                                     _stream(stream)))
 
     @property
     def trace_stride(self) -> int:

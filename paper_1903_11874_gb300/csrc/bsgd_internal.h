@@ -215,6 +215,10 @@ struct SolveDev {
     void *xT;          // image, [z][x][y], storage type
     float *gT;         // their part of the aggregated gradient, [z][x][y]
     double *eud;       // Algorithm 3: effective update direction of the window (or null)
+    // owner-computes sharding: 1 for the column blocks this process owns; the
+    // FP, BP and update of a pair whose block it does not own are skipped
+    // (null: every block is owned)
+    const unsigned char *owned;
 };
 
 // Host tables of a geometry (rays, blocks, bands, compact band offsets) without

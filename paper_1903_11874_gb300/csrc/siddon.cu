@@ -199,6 +199,7 @@ __device__ __forceinline__ void fp_solve_body(const DeviceGeom &G, const SolveDe
     int a, i, j, u, v;
     bool act;
     if (!solve_pixel(G, S, tile, slot, p, a, i, j, u, v, act)) return;
+    if (S.owned && !S.owned[j]) return;   // another process owns block j
     float zn = 0.f;
     if (act) {
         const bool yf = S.xT != nullptr && G.view_yfast[a];
@@ -249,6 +250,7 @@ __device__ __forceinline__ void bp_solve_body(const DeviceGeom &G, const SolveDe
     int a, i, j, u, v;
     bool act;
     if (!solve_pixel(G, S, tile, slot, p, a, i, j, u, v, act) || !act) return;
+    if (S.owned && !S.owned[j]) return;   // another process owns block j
     const int64_t row = ((int64_t)a * G.nv + v) * G.nu + u;
     const T *r = reinterpret_cast<const T *>(S.r);
     T *rt = reinterpret_cast<T *>(S.rt);

@@ -295,15 +295,9 @@ __global__ void pair_updates_kernel(const DeviceGeom G, const unsigned long long
 // kResRows detector rows of one view.
 constexpr int kResRows = 4;
 
-template <typename T>
-__global__ void __launch_bounds__(256) residual_kernel(const DeviceGeom G, const SolveDev S) {
-    const Work &W = *S.work;
-    const int rb = blockIdx.z;
-    if (rb >= W.n_rows) return;
-    const int i = W.rows[rb];
-    const int slot = blockIdx.y;
-    if (slot >= G.block_nviews[i]) return;
-    const int a = G.block_views[i * G.max_views + slot];
+// Bounding box, at view a, of the bands of the iteration's column blocks: the
+// rows whose z^j changed (the residual pass and the sharded exchange cover it).
+__device__ __forceinline__ Band union_band(const DeviceGeom &G, const Work &W, int a) {
     Band b{1 << 30, -1, 1 << 30, -1};
     for (int c = 0; c < W.n_cols; ++c) {
         const Band q = G.bands[(size_t)a * (G.N + 1) + W.cols[c]];
@@ -313,6 +307,19 @@ __global__ void __launch_bounds__(256) residual_kernel(const DeviceGeom G, const
         b.v0 = min(b.v0, q.v0);
         b.v1 = max(b.v1, q.v1);
     }
+    return b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) residual_kernel(const DeviceGeom G, const SolveDev S) {
+    const Work &W = *S.work;
+    const int rb = blockIdx.z;
+    if (rb >= W.n_rows) return;
+    const int i = W.rows[rb];
+    const int slot = blockIdx.y;
+    if (slot >= G.block_nviews[i]) return;
+    const int a = G.block_views[i * G.max_views + slot];
+    const Band b = union_band(G, W, a);
     const int vbeg = b.v0 + blockIdx.x * kResRows;
     if (b.u0 > b.u1 || vbeg > b.v1) return;
     const T *y = reinterpret_cast<const T *>(S.y);
@@ -331,6 +338,82 @@ __global__ void __launch_bounds__(256) residual_kernel(const DeviceGeom G, const
                 if (in) zs += ldv(z + kz);
             }
             const float rn = rnd(ldf(y + row) - zs, r);
+            const float ro = ldv(r + row);
+            if (rn != ro) {
+                stf(r + row, rn);
+                dn += (double)rn * rn - (double)ro * ro;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = dn;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+            if (t != 0.0) atomicAdd(S.S + (size_t)i * G.nv + v, t);
+        }
+    }
+}
+
+// Owner-computes sharding (one process per device, each owning some column
+// blocks): the exchange buffer holds, for every row of the union band in each
+// view of each drawn row block, this process's part sum_{owned j} z^j of
+// sum_j z^j. The processes sum their buffers (one all-reduce), then each forms
+// r = y - sum_j z^j from the total. Layout: [row-block slot][view slot][v][u].
+__device__ __forceinline__ int64_t xchg_index(const DeviceGeom &G, int rb, int slot, int v, int u) {
+    return (((int64_t)rb * G.max_views + slot) * G.nv + v) * G.nu + u;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) shard_partial_kernel(const DeviceGeom G, const SolveDev S,
+                                                            float *__restrict__ xchg) {
+    const Work &W = *S.work;
+    const int rb = blockIdx.z;
+    if (rb >= W.n_rows) return;
+    const int i = W.rows[rb], slot = blockIdx.y;
+    if (slot >= G.block_nviews[i]) return;
+    const int a = G.block_views[i * G.max_views + slot];
+    const Band b = union_band(G, W, a);
+    const int vbeg = b.v0 + blockIdx.x * kResRows;
+    if (b.u0 > b.u1 || vbeg > b.v1) return;
+    const T *z = reinterpret_cast<const T *>(S.z);
+    for (int v = vbeg; v < vbeg + kResRows && v <= b.v1; ++v)
+        for (int u = b.u0 + threadIdx.x; u <= b.u1; u += blockDim.x) {
+            float zs = 0.f;
+            for (int jj = 0; jj < G.N; ++jj) {
+                if (!S.owned[jj]) continue;
+                bool in;
+                const int64_t kz = zslot(G, jj, a, u, v, in);
+                if (in) zs += ldv(z + kz);
+            }
+            xchg[xchg_index(G, rb, slot, v, u)] = zs;
+        }
+}
+
+// r = y - (the all-reduced sum of z^j) over the same rows, with the FP64
+// residual table updated by the change of r^2.
+template <typename T>
+__global__ void __launch_bounds__(256) shard_residual_kernel(const DeviceGeom G, const SolveDev S,
+                                                             const float *__restrict__ xchg) {
+    const Work &W = *S.work;
+    const int rb = blockIdx.z;
+    if (rb >= W.n_rows) return;
+    const int i = W.rows[rb], slot = blockIdx.y;
+    if (slot >= G.block_nviews[i]) return;
+    const int a = G.block_views[i * G.max_views + slot];
+    const Band b = union_band(G, W, a);
+    const int vbeg = b.v0 + blockIdx.x * kResRows;
+    if (b.u0 > b.u1 || vbeg > b.v1) return;
+    const T *y = reinterpret_cast<const T *>(S.y);
+    T *r = reinterpret_cast<T *>(S.r);
+    __shared__ double sh[8];
+    for (int v = vbeg; v < vbeg + kResRows && v <= b.v1; ++v) {
+        const int64_t base = ((int64_t)a * G.nv + v) * G.nu;
+        double dn = 0.0;
+        for (int u = b.u0 + threadIdx.x; u <= b.u1; u += blockDim.x) {
+            const int64_t row = base + u;
+            const float rn = rnd(ldf(y + row) - xchg[xchg_index(G, rb, slot, v, u)], r);
             const float ro = ldv(r + row);
             if (rn != ro) {
                 stf(r + row, rn);
@@ -379,6 +462,7 @@ __device__ void update_body(const DeviceGeom &G, const SolveDev &S, T *__restric
     const Work &W = *S.work;
     if (c >= W.n_cols) return;
     const int j = W.cols[c];
+    if (S.owned && !S.owned[j]) return;   // another process owns block j
     const float mu = (float)*S.mu;
     if (S.gT == nullptr) {
         const int64_t b0 = (int64_t)G.plane_start[j] * G.plane_stride;
@@ -753,6 +837,7 @@ struct bsgd_state {
     int *cells = nullptr, *wband = nullptr;
     int64_t *d_iter = nullptr;
     int *x0_flag = nullptr;     // warm start: 1 if the starting image is not zero
+    unsigned char *owned = nullptr;  // owner-computes sharding: owned column blocks (N)
     int32_t *trace = nullptr, *replay = nullptr;
     int64_t replay_start = 0, replay_n = 0;
     unsigned long long *counts = nullptr, *updates = nullptr;
@@ -873,8 +958,8 @@ static void free_state(bsgd_state *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     // counts and cw belong to the geometry's cache; replay is a plain allocation
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->x0_flag, s->trace, s->updates, s->pair_upd, s->eud,
-                    s->eud_prev, s->am_part, s->am};
+                    s->wband, s->d_iter, s->x0_flag, s->owned, s->trace, s->updates, s->pair_upd,
+                    s->eud, s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) pfree(p);
     cudaFree(s->replay);
     tv_work_free(s->tv);
@@ -1157,7 +1242,7 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         (e = palloc((void **)&s->trace, 4 * (size_t)s->trace_cap * s->stride, st)) ||
         (e = palloc((void **)&s->updates, 8, st)) ||
         (e = palloc((void **)&s->pair_upd, 8 * (size_t)M * N, st)) ||
-        (s->st != BSGD_F32 && (e = palloc(&s->xlo, C * es, st))) ||
+        (s->st != BSGD_F32 && !p->image_plain && (e = palloc(&s->xlo, C * es, st))) ||
         (g->desc.nz > 1 && (e = palloc(&s->xT, C * es, st))) ||
         (g->desc.nz > 1 && (e = palloc((void **)&s->gT, C * 4, st))) ||
         (p->tv_lambda > 0 && (e = tv_work_alloc(g, s->tv))) ||
@@ -1265,8 +1350,8 @@ void state_release(bsgd_state *s, cudaStream_t st) {
     }
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->x0_flag, s->trace, s->updates, s->pair_upd, s->eud,
-                    s->eud_prev, s->am_part, s->am};
+                    s->wband, s->d_iter, s->x0_flag, s->owned, s->trace, s->updates, s->pair_upd,
+                    s->eud, s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) pool_free(p, st);
     delete s;
 }
@@ -1373,7 +1458,7 @@ size_t state_bytes(const bsgd_geometry_desc &d, int M, int N, const bsgd_solve_p
     size_t b = 0;
     b += R * es * 2 + Z * es * 2;                      // y, r, z^j, r~^j
     b += C * 4;                                        // g
-    if (es != 4) b += C * es;                          // low-order image term
+    if (es != 4 && !p.image_plain) b += C * es;        // low-order image term
     if (d.nz > 1) b += C * (es + 4);                   // y-fastest copies of x and g
     b += 8 * (size_t)M * d.nv;                         // residual table
     b += 4 * (size_t)kMaxPairs * maxV + 8 * (size_t)M * N + sizeof(Work) + 64;
@@ -1401,6 +1486,39 @@ static bsgd_status sync_xT(bsgd_state *s, void *x, cudaStream_t st) {
     if (s->st == BSGD_F32) transpose_kernel<float><<<gb, 256, 0, st>>>(g->dg, (const float *)x, (float *)s->xT);
     else if (s->st == BSGD_BF16) transpose_kernel<__nv_bfloat16><<<gb, 256, 0, st>>>(g->dg, (const __nv_bfloat16 *)x, (__nv_bfloat16 *)s->xT);
     else transpose_kernel<__half><<<gb, 256, 0, st>>>(g->dg, (const __half *)x, (__half *)s->xT);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+// The block update x_J += mu g_J of iteration s->iters (its work list); with
+// draw_next, one extra CTA draws the next iteration's blocks.
+static bsgd_status launch_update(bsgd_state *s, void *x, cudaStream_t st, bool draw_next) {
+    const bsgd_geometry *g = s->g;
+    const int64_t k = s->iters;
+    int64_t maxJ = 0;
+    for (int j = 0; j < g->N; ++j) maxJ = std::max(maxJ, g->block_cols(j));
+    // with the y-fastest copies: one CTA per 32 x 32 tile of the slab
+    const int64_t nt = s->gT ? ((g->desc.nx + 31) / 32) * (int64_t)((g->desc.ny + 31) / 32) *
+                                   ((maxJ + (int64_t)g->desc.nx * g->desc.ny - 1) / ((int64_t)g->desc.nx * g->desc.ny))
+                             : (maxJ + 1023) / 1024;
+    dim3 ug((unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, 65535)), s->kN);
+    if (draw_next) {
+        // the draw of iteration k + 1 needs only the residual table, final
+        // once this iteration's FPs are done: one extra CTA of the update
+        SampleArgs An;
+        fill_sample_args(s, An, k + 1);
+        dim3 ugs(ug.x + 1, ug.y);
+        if (s->st == BSGD_F32)
+            update_sample_kernel<float><<<ugs, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr, An);
+        else if (s->st == BSGD_BF16)
+            update_sample_kernel<__nv_bfloat16><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo, An);
+        else
+            update_sample_kernel<__half><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo, An);
+    } else {
+        if (s->st == BSGD_F32) update_kernel<float><<<ug, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr);
+        else if (s->st == BSGD_BF16) update_kernel<__nv_bfloat16><<<ug, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo);
+        else update_kernel<__half><<<ug, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo);
+    }
     BSGD_CUDA(cudaGetLastError());
     return BSGD_OK;
 }
@@ -1454,32 +1572,8 @@ static bsgd_status one_iteration(bsgd_state *s, void *x, cudaStream_t st, bool d
         BSGD_TRY(launch_bp_solve(g, s->dev, s->st, s->P, s->max_tiles, st));
         stage_end(s, BSGD_STAGE_BP, b, 1, st);
     }
-    int64_t maxJ = 0;
-    for (int j = 0; j < g->N; ++j) maxJ = std::max(maxJ, g->block_cols(j));
-    // with the y-fastest copies: one CTA per 32 x 32 tile of the slab
-    const int64_t nt = s->gT ? ((g->desc.nx + 31) / 32) * (int64_t)((g->desc.ny + 31) / 32) *
-                                   ((maxJ + (int64_t)g->desc.nx * g->desc.ny - 1) / ((int64_t)g->desc.nx * g->desc.ny))
-                             : (maxJ + 1023) / 1024;
-    dim3 ug((unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, 65535)), s->kN);
     b = stage_begin(s, st);
-    if (draw_next) {
-        // the draw of iteration k + 1 needs only the residual table, final
-        // once this iteration's FPs are done: one extra CTA of the update
-        SampleArgs An;
-        fill_sample_args(s, An, k + 1);
-        dim3 ugs(ug.x + 1, ug.y);
-        if (s->st == BSGD_F32)
-            update_sample_kernel<float><<<ugs, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr, An);
-        else if (s->st == BSGD_BF16)
-            update_sample_kernel<__nv_bfloat16><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo, An);
-        else
-            update_sample_kernel<__half><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo, An);
-    } else {
-        if (s->st == BSGD_F32) update_kernel<float><<<ug, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr);
-        else if (s->st == BSGD_BF16) update_kernel<__nv_bfloat16><<<ug, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo);
-        else update_kernel<__half><<<ug, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo);
-    }
-    BSGD_CUDA(cudaGetLastError());
+    BSGD_TRY(launch_update(s, x, st, draw_next));
     stage_end(s, BSGD_STAGE_UPDATE, b, 1, st);
     s->iters += 1;
     if (s->auto_win > 0 && s->iters % ((int64_t)s->epoch_len * s->auto_win) == 0) {
@@ -1523,6 +1617,7 @@ extern "C" bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void
     if (!s || !x) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
     if (n_iters < 0) return fail(BSGD_ERR_INVALID_ARG, "n_iters < 0");
     cudaStream_t st = (cudaStream_t)stream;
+    if (s->owned) return fail(BSGD_ERR_STATE, "a sharded state steps through bsgd_shard_begin / _end");
     if (n_iters > 0) BSGD_TRY(sync_xT(s, x, st));
     if (n_iters > 0 && s->iters == 0) BSGD_TRY(warm_start(s, x, st));
     for (int k = 0; k < n_iters; ++k) BSGD_TRY(one_iteration(s, x, st, k > 0, k + 1 < n_iters));
@@ -1548,6 +1643,88 @@ extern "C" bsgd_status bsgd_state_query(bsgd_state *s, bsgd_report *out, void *s
     out->epoch = (double)s->iters / s->epoch_len;
     out->updates = (int64_t)upd;
     return BSGD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Owner-computes sharding (Sec. 2, Fig. 1: the nodes hold column blocks x_J and
+// the master sums their A_I^J x_J into r_I). Every process holds a state of the
+// whole problem but computes only for the column blocks it owns; one iteration
+// is bsgd_shard_begin (draw, FP of the owned drawn pairs, the process's part of
+// sum_j z^j on the rows that changed), a sum of the exchange buffers over the
+// processes (the caller's all-reduce), and bsgd_shard_end (r from the total, BP
+// of the owned drawn pairs, update of the owned drawn blocks).
+
+extern "C" bsgd_status bsgd_state_set_shard(bsgd_state *s, const int32_t *owned_blocks, int n_owned,
+                                            int64_t *exchange_len) {
+    if (!s || (!owned_blocks && n_owned > 0) || !exchange_len)
+        return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (s->iters != 0) return fail(BSGD_ERR_STATE, "shard a state before its first iteration");
+    if (s->p.pair_sampling != BSGD_PAIRS_UNIFORM || s->p.cells == BSGD_CELLS_GEOMETRIC ||
+        s->p.tv_lambda > 0 || s->am || s->replay)
+        return fail(BSGD_ERR_INVALID_ARG,
+                    "sharded states draw uniform pairs (whole views or uniform cells), with no TV "
+                    "prox, no automatic step and no replay");
+    const bsgd_geometry *g = s->g;
+    if (n_owned < 0 || n_owned > g->N) return fail(BSGD_ERR_INVALID_ARG, "n_owned out of range");
+    std::vector<unsigned char> m(g->N, 0);
+    for (int k = 0; k < n_owned; ++k) {
+        if (owned_blocks[k] < 0 || owned_blocks[k] >= g->N)
+            return fail(BSGD_ERR_INVALID_ARG, "owned block id out of range");
+        m[owned_blocks[k]] = 1;
+    }
+    if (!s->owned) {
+        BSGD_TRY(palloc((void **)&s->owned, g->N, 0));
+        BSGD_CUDA(cudaStreamSynchronize(0));
+    }
+    BSGD_CUDA(cudaMemcpy(s->owned, m.data(), g->N, cudaMemcpyHostToDevice));
+    s->dev.owned = s->owned;
+    *exchange_len = (int64_t)s->kM * g->max_views * g->desc.nv * g->desc.nu;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_shard_begin(bsgd_state *s, void *x, float *exchange, void *stream) {
+    if (!s || !x || !exchange) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (!s->owned) return fail(BSGD_ERR_STATE, "not a sharded state (bsgd_state_set_shard)");
+    const bsgd_geometry *g = s->g;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t k = s->iters;
+    if (k == 0) BSGD_TRY(sync_xT(s, x, st));
+    s->dev.work = work_buf(s, k);
+    s->dev.cells = cells_buf(s, k);
+    SampleArgs A;
+    fill_sample_args(s, A, k);
+    sample_kernel<<<1, kSampleThreads, 0, st>>>(A);
+    BSGD_CUDA(cudaGetLastError());
+    if (s->max_tiles > 0) BSGD_TRY(launch_fp_solve(g, s->dev, x, s->st, s->P, s->max_tiles, false, st));
+    dim3 grid((g->desc.nv + kResRows - 1) / kResRows, g->max_views, s->kM);
+    if (s->st == BSGD_F32) shard_partial_kernel<float><<<grid, 256, 0, st>>>(g->dg, s->dev, exchange);
+    else if (s->st == BSGD_BF16) shard_partial_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(g->dg, s->dev, exchange);
+    else shard_partial_kernel<__half><<<grid, 256, 0, st>>>(g->dg, s->dev, exchange);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_shard_end(bsgd_state *s, void *x, const float *exchange, void *stream) {
+    if (!s || !x || !exchange) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (!s->owned) return fail(BSGD_ERR_STATE, "not a sharded state (bsgd_state_set_shard)");
+    const bsgd_geometry *g = s->g;
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid((g->desc.nv + kResRows - 1) / kResRows, g->max_views, s->kM);
+    if (s->st == BSGD_F32) shard_residual_kernel<float><<<grid, 256, 0, st>>>(g->dg, s->dev, exchange);
+    else if (s->st == BSGD_BF16) shard_residual_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(g->dg, s->dev, exchange);
+    else shard_residual_kernel<__half><<<grid, 256, 0, st>>>(g->dg, s->dev, exchange);
+    BSGD_CUDA(cudaGetLastError());
+    if (s->max_tiles > 0) BSGD_TRY(launch_bp_solve(g, s->dev, s->st, s->P, s->max_tiles, st));
+    BSGD_TRY(launch_update(s, x, st, false));
+    s->iters += 1;
+    return BSGD_OK;
+}
+
+extern "C" bsgd_status bsgd_state_read_residual(bsgd_state *s, void *out, bsgd_dtype ot,
+                                                void *stream) {
+    if (!s || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (!dtype_ok(ot)) return fail(BSGD_ERR_INVALID_ARG, "bad dtype");
+    return convert(s->r, s->st, out, ot, s->g->n_rows(), (cudaStream_t)stream);
 }
 
 extern "C" bsgd_status bsgd_state_profile(bsgd_state *s, int enable) {

@@ -87,3 +87,29 @@ def uniform_array(shape, seed: int, lo: float = 0.0, hi: float = 1.0, dtype=np.f
 
 def normal_array(shape, seed: int, dtype=np.float64) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal(size=shape).astype(dtype)
+
+
+# Reduced precision workload: the 512^3 / 720-view / 512^2-detector BSGD-TV
+# set-up at 1/8 of its resolution in every dimension (the same 256 mm volume,
+# 409.6 mm detector, DSO 500 / DSD 1000 mm), 16 x 16 blocks, one pair per
+# iteration, uniform draws, lambda = 1e-3 with 20 FGP iterations per epoch,
+# noise-free data of a kappa-scaled ellipsoid phantom, 10 epochs. The FP64
+# oracle finishes it in a minute or two; its image after every epoch is kept at
+# n_samples seeded voxels (sample_indices) for the bench's comparison.
+PRECISION_REDUCED = dict(
+    geometry=dict(kind="cone3d", nx=64, ny=64, nz=64, dx=4.0, dy=4.0, dz=4.0, n_views=90,
+                  nu=64, nv=64, du=6.4, dv=6.4, dso=500.0, dsd=1000.0),
+    M=16, N=16, tv_lambda=1e-3, tv_iters=20, epochs=10, seed=1, rho=0.25, power_iters=30,
+    phantom_seed=0, n_ellipsoids=10, kappa=0.01, n_samples=512, sample_seed=11,
+)
+
+
+def precision_reduced_phantom() -> np.ndarray:
+    w = PRECISION_REDUCED
+    g = w["geometry"]
+    return ellipsoid_phantom(g["nx"], g["ny"], g["nz"], w["n_ellipsoids"], w["phantom_seed"]) * w["kappa"]
+
+
+def sample_indices(n: int, k: int, seed: int) -> np.ndarray:
+    """k distinct voxel indices of [0, n), sorted."""
+    return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False))
