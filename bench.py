@@ -335,6 +335,10 @@ def run_cuda(args):
                "h2d_bytes_per_step": int(gg.n_rows * 4), "d2h_bytes_per_step": int(gg.n_cols * 4),
                "api": "bsgd_solve (1 epoch per call from x0 = 0 (zero_start), pinned host y and x, fixed mu)"}
 
+    full_solve = None
+    if not args.no_e2e and rank == 0 and world == 1:
+        full_solve = full_solve_leg(B, torch, y_np)
+
     extra = None
     if not args.no_extra and rank == 0 and world == 1:
         extra = extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks)
@@ -375,13 +379,58 @@ def run_cuda(args):
             "gpu_launches": int(launches), "stages_ms": stages,
             "ms_per_step_profiled": round(ms_profiled / args.steps, 3),
             "kernels": "split FP / BP" if args.split else "fused FP+residual+BP",
-            "roofline": roofline, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roofline, "clocks": clk, "e2e": e2e, "e2e_full_solve": full_solve,
+            "cpu_baseline": cpu,
             "serving": serving, "paper_scale": paper, "rows": extra,
         }
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def full_solve_leg(B, torch, y_np, n_solves=5, epochs=20):
+    """The whole configuration-2 reconstruction as one user call: bsgd_solve
+    with the STRIP step rule (its FP64 power iteration inside the call), 20
+    epochs of residual-weighted pairs, pinned host y and x. `cold`: the first
+    call on a new geometry (geometry tables, update-count pass and power
+    iteration included); then n_solves calls on that geometry (the step's
+    Lipschitz estimate and the update counts are kept with it), p50 / p99 of
+    their latency, and the same request served by a bsgd_server one at a time."""
+    import numpy as np
+    yh = torch.from_numpy(y_np).pin_memory()
+    xh = torch.zeros(int(np.prod([GEOM["nx"], GEOM["ny"], GEOM["nz"]])), dtype=torch.float32).pin_memory()
+    prm = B.SolveParams(alpha=1 / M, gamma=1 / N, epochs=epochs, step_rule=B.STEP_STRIP, rho=RHO,
+                        power_iters=30, pair_sampling=B.PAIRS_RESIDUAL, seed=1, zero_start=True)
+    t0 = time.perf_counter()
+    gg = B.Geometry(M=M, N=N, **GEOM)
+    rep = B.bsgd_solve(gg, prm, yh, xh)
+    cold = time.perf_counter() - t0
+    lat, upd = [], 0
+    for _ in range(n_solves):
+        t0 = time.perf_counter()
+        rep = B.bsgd_solve(gg, prm, yh, xh)
+        lat.append(time.perf_counter() - t0)
+        upd += rep["updates"]
+    srv = B.Server(budget_bytes=16 << 30, max_slots=4)
+    slat = []
+    try:
+        yn = np.ascontiguousarray(y_np)
+        srv.wait(srv.submit(GEOM, M, N, prm, yn), timeout_ms=600000)     # warm-up
+        for _ in range(n_solves):
+            t0 = time.perf_counter()
+            srv.wait(srv.submit(GEOM, M, N, prm, yn), timeout_ms=600000)
+            slat.append(time.perf_counter() - t0)
+    finally:
+        srv.close()
+    q = lambda v, f: sorted(v)[min(len(v) - 1, int(math.floor(f * (len(v) - 1) + 0.5)))]
+    return {"epochs": epochs, "step_rule": "STRIP (rho %.2f, 30 power iterations)" % RHO,
+            "cold_first_call_ms": round(cold * 1e3, 1),
+            "p50_ms": round(q(lat, 0.5) * 1e3, 1), "p99_ms": round(q(lat, 0.99) * 1e3, 1),
+            "value": round(upd / sum(lat) / 1e9, 3), "unit": UNIT,
+            "served_alone_p50_ms": round(q(slat, 0.5) * 1e3, 1),
+            "served_alone_p99_ms": round(q(slat, 0.99) * 1e3, 1),
+            "calls": n_solves, "residual_norm_end": rep["residual_norm"], "mu": rep["mu"]}
 
 
 # ---------------------------------------------------------------------------
@@ -802,11 +851,58 @@ def oracle_sample(y_np, mu, n_iters):
     return upd, dt, OP.num_threads()
 
 
+# One epoch (16 block iterations) of the 64^2 parallel-beam set-up (90 views,
+# 96 bins, 4 x 4 blocks) by the FP64 oracle, run in a child process so that its
+# OpenMP thread count can be set; prints {"updates", "seconds", "threads"}.
+_CONFIG1_EPOCH = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import bsgd as OB
+from oracle import projector as OP
+from paper_1903_11874_gb300 import synth
+og = OP.Geometry("par2d", 64, 64, 1, 1.0, 1.0, 1.0, 90, 96, 1, 1.0, 1.0)
+y = OP.fp(og, synth.ellipse_phantom(64, 64, 6, 0).reshape(-1)).reshape(-1)
+prm = OB.Params(4, 4, 0.25, 0.25, 1e-3, seed=1)
+st = OB.BSGDState(og, y, prm)
+st.step()
+t0 = time.perf_counter()
+for _ in range(16):
+    st.step()
+dt = time.perf_counter() - t0
+upd = 0
+for sel in st.history[1:]:
+    for (i, j) in sel.pairs:
+        upd += 2 * OP.count_rows(og, OP.rows_of_views(og, OP.row_block_views(og, 4, i)),
+                                 OP.column_block(og, 4, j))
+print(json.dumps({"updates": upd, "seconds": dt, "threads": OP.num_threads()}))
+"""
+
+
+def oracle_config1_epoch(threads):
+    env = dict(os.environ)
+    if threads:
+        env["OMP_NUM_THREADS"] = str(threads)
+    r = subprocess.run([sys.executable, "-c", _CONFIG1_EPOCH % os.path.dirname(os.path.abspath(__file__))],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return None
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": round(d["updates"] / d["seconds"] / 1e9, 5), "unit": UNIT,
+            "cores": d["threads"], "epoch_s": round(d["seconds"], 4)}
+
+
 def cpu_baseline(y_np, mu, n_iters):
     upd, dt, threads = oracle_sample(y_np, mu, n_iters)
     return {"value": round(upd / dt / 1e9, 5), "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d BSGD iterations (one (row block, z-slab) pair each) of the workload, "
-                      "FP64 oracle, %.1f s" % (n_iters, dt)}
+                      "FP64 oracle, %.1f s" % (n_iters, dt),
+            # an epoch is 64 such iterations; the oracle's time per iteration does
+            # not depend on the iteration (each walks one pair's rays), so one
+            # epoch is extrapolated from the sample
+            "epoch_s_extrapolated": round(dt / n_iters * ITERS_PER_EPOCH, 1),
+            "config1_epoch": {"all_cores": oracle_config1_epoch(None),
+                              "single_thread": oracle_config1_epoch(1)}}
 
 
 def run_reference(args):

@@ -311,7 +311,10 @@ typedef struct {
  * Initial state is Algorithm 1's: g = 0, z = 0, r = y, for the starting image
  * x0 = 0; the first bsgd_block_step takes the x it is given as x0 and, when
  * x0 is not zero, sets z^j = A^j x0_J and r = y - sum_j z^j first (see there).
- * Computes mu by power iteration for the STRIP / BLOCK rules. Synchronous.
+ * Computes mu by power iteration for the STRIP / BLOCK rules; the largest
+ * Lipschitz estimate is kept with the geometry (per rule and power_iters), so
+ * later states on the same geometry take mu = rho / (that estimate) without
+ * iterating again. Synchronous.
  * Memory: the state's arrays come from a stream-ordered pool per device, owned
  * by the library, that keeps up to 32 GiB of freed memory for reuse by later
  * states (so a state per call costs no page mapping once the pool is warm); the

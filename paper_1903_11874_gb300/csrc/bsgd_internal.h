@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 
 #include <cstdint>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -112,6 +113,11 @@ struct bsgd_geometry {
     mutable std::mutex cache_mu;
     mutable unsigned long long *d_counts[5] = {};
     mutable double *d_cw[5] = {};
+    // Largest block Lipschitz estimate max ||A^J||^2 (STRIP) or max ||A_I^J||^2
+    // (BLOCK) by power_iters power-iteration steps: a property of the geometry,
+    // kept so that later states on it need no power iteration (key: rule,
+    // power_iters).
+    mutable std::map<std::pair<int, int>, double> lambda_cache;
 
     int64_t n_rows() const { return (int64_t)desc.n_views * desc.nv * desc.nu; }
     int64_t n_cols() const { return (int64_t)desc.nx * desc.ny * desc.nz; }
@@ -322,12 +328,21 @@ struct ReqDesc {
     int64_t max_block_cols;  // voxels of the largest column block
 };
 
+// The round's work items come in classes, each run by its own persistent
+// kernel (so that each gets the registers, and the occupancy, of its own pass):
+// class = 3 * (several column blocks per iteration ? 1 : 0) + storage type.
+// Table entries of class c are [lo[c], hi[c]) (the table is sorted by class);
+// a request's work_begin counts within its class. Only the kernels of the
+// classes present are in the round's graph.
+constexpr int kRoundClasses = 6;
 struct RoundCtl {
-    unsigned long long next;               // persistent-kernel work counter
-    int n;                                 // table entries in use
+    unsigned long long next[kRoundClasses];  // persistent-kernel work counters
+    int n;                                   // table entries in use
     int pad;
-    int64_t total_items;                   // FP / BP work items of the round
+    int lo[kRoundClasses], hi[kRoundClasses];
+    int64_t total_items[kRoundClasses];      // FP / BP work items of the round, per class
 };
+__host__ __device__ inline int round_class(int kN, int dtype) { return 3 * (kN > 1 ? 1 : 0) + dtype; }
 
 // Fill a request descriptor from a live state (solver.cu).
 bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out);
@@ -342,9 +357,9 @@ bsgd_status convert(const void *in, bsgd_dtype it, void *out, bsgd_dtype ot, int
 // Round kernels of the server (enqueued once into a captured graph).
 bsgd_status launch_round_sample(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
                                 cudaStream_t st);
-bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st);
+bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int cls, int grid, cudaStream_t st);
 bsgd_status launch_round_update(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
                                 cudaStream_t st);
-int round_persistent_grid();
+int round_persistent_grid(int cls);
 
 }  // namespace bsgd

@@ -8,9 +8,11 @@
 //              step is reused) and hands the ready request to the round thread;
 //   rounds     keeps a device table of the resident requests and replays one
 //              captured CUDA graph per round: sampler of every request, then
-//              one persistent kernel (FP, residual and BP of each ray) that
-//              shares all requests' detector tiles through an atomic work
-//              counter, then every request's block update. After the last iteration of a request the round thread
+//              persistent kernels (FP, residual and BP of each ray; one per
+//              class of request present: one or several column blocks per
+//              iteration x storage type) that share all requests' detector
+//              tiles through atomic work counters, then every request's block
+//              update. After the last iteration of a request the round thread
 //              copies its image out, and once that copy has finished it frees
 //              the request and releases its budget.
 // The graph never changes: the kernels read the table and the number of
@@ -105,8 +107,9 @@ struct bsgd_server {
     RoundCtl *d_ctl = nullptr;
     ReqDesc *h_table = nullptr;   // pinned
     RoundCtl *h_ctl = nullptr;    // pinned
-    cudaGraphExec_t graph = nullptr;
-    int grid = 0;
+    std::map<int, cudaGraphExec_t> graphs;   // round graph per set of classes present
+    int class_mask = 0;                      // classes of the current table
+    int grid[kRoundClasses] = {};   // persistent grid of each class's kernel
     // stats
     int64_t submitted = 0, admitted = 0, completed = 0, failed = 0, rounds = 0;
     int peak_resident = 0;
@@ -350,19 +353,30 @@ void admission_loop(bsgd_server *S, cudaStream_t stream) {
     }
 }
 
-bsgd_status build_graph(bsgd_server *S) {
+// The round graph for a set of request classes (bit c = class c present):
+// sampler, the persistent kernel of each present class, block updates.
+bsgd_status round_graph(bsgd_server *S, int mask, cudaGraphExec_t *out) {
+    auto it = S->graphs.find(mask);
+    if (it != S->graphs.end()) {
+        *out = it->second;
+        return BSGD_OK;
+    }
     cudaGraph_t graph = nullptr;
     BSGD_CUDA(cudaStreamBeginCapture(S->round_stream, cudaStreamCaptureModeThreadLocal));
-    cudaMemsetAsync(&S->d_ctl->next, 0, sizeof(unsigned long long), S->round_stream);
+    cudaMemsetAsync(&S->d_ctl->next[0], 0, kRoundClasses * sizeof(unsigned long long), S->round_stream);
     bsgd_status st = launch_round_sample(S->d_table, S->d_ctl, S->prm.max_slots, S->round_stream);
-    if (!st) st = launch_round_solve(S->d_table, S->d_ctl, S->grid, S->round_stream);
+    for (int c = 0; c < kRoundClasses && !st; ++c)
+        if (mask & (1 << c)) st = launch_round_solve(S->d_table, S->d_ctl, c, S->grid[c], S->round_stream);
     if (!st) st = launch_round_update(S->d_table, S->d_ctl, S->prm.max_slots, S->round_stream);
     cudaError_t e = cudaStreamEndCapture(S->round_stream, &graph);
     BSGD_TRY(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&S->graph, graph, 0);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    S->graphs[mask] = exec;
+    *out = exec;
     return BSGD_OK;
 }
 
@@ -370,18 +384,27 @@ bsgd_status build_graph(bsgd_server *S) {
 // flight: the round stream is synchronised first).
 bsgd_status upload_table(bsgd_server *S) {
     BSGD_CUDA(cudaStreamSynchronize(S->round_stream));
-    int64_t begin = 0;
-    int n = 0;
-    for (Request *r : S->resident) {
-        ReqDesc d;
-        BSGD_TRY(state_descriptor(r->st, r->x, &d));
-        d.work_begin = begin;
-        begin += d.work_count;
-        S->h_table[n++] = d;
+    // sorted by class (round_class: one or several column blocks per
+    // iteration x storage type); work items are numbered within each class
+    int n = 0, mask = 0;
+    for (int cls = 0; cls < kRoundClasses; ++cls) {
+        int64_t begin = 0;
+        S->h_ctl->lo[cls] = n;
+        for (Request *r : S->resident) {
+            ReqDesc d;
+            BSGD_TRY(state_descriptor(r->st, r->x, &d));
+            if (round_class(d.kN, d.dtype) != cls) continue;
+            d.work_begin = begin;
+            begin += d.work_count;
+            S->h_table[n++] = d;
+        }
+        S->h_ctl->hi[cls] = n;
+        S->h_ctl->total_items[cls] = begin;
+        S->h_ctl->next[cls] = 0;
+        if (S->h_ctl->hi[cls] > S->h_ctl->lo[cls]) mask |= 1 << cls;
     }
     S->h_ctl->n = n;
-    S->h_ctl->total_items = begin;
-    S->h_ctl->next = 0;
+    S->class_mask = mask;
     if (n) BSGD_CUDA(cudaMemcpyAsync(S->d_table, S->h_table, sizeof(ReqDesc) * n,
                                      cudaMemcpyHostToDevice, S->round_stream));
     BSGD_CUDA(cudaMemcpyAsync(S->d_ctl, S->h_ctl, sizeof(RoundCtl), cudaMemcpyHostToDevice,
@@ -447,7 +470,8 @@ void round_loop(bsgd_server *S) {
             dirty = false;
         }
         if (!S->resident.empty()) {
-            cudaGraphLaunch(S->graph, S->round_stream);
+            cudaGraphExec_t graph = nullptr;
+            if (round_graph(S, S->class_mask, &graph) == BSGD_OK) cudaGraphLaunch(graph, S->round_stream);
             S->rounds++;
             std::vector<Request *> leaving;
             for (Request *r : S->resident)
@@ -558,13 +582,12 @@ extern "C" bsgd_status bsgd_server_create(const bsgd_server_params *p, bsgd_serv
         BSGD_CUDA(cudaHostAlloc((void **)&S->h_ctl, sizeof(RoundCtl), cudaHostAllocDefault));
         std::memset(S->h_ctl, 0, sizeof(RoundCtl));
         BSGD_CUDA(cudaMemset(S->d_ctl, 0, sizeof(RoundCtl)));
-        S->grid = round_persistent_grid();
-        BSGD_TRY(build_graph(S));
+        for (int c = 0; c < kRoundClasses; ++c) S->grid[c] = round_persistent_grid(c);
         return BSGD_OK;
     };
     bsgd_status st = init();
     if (st) {
-        if (S->graph) cudaGraphExecDestroy(S->graph);
+        for (auto &kv : S->graphs) cudaGraphExecDestroy(kv.second);
         cudaFree(S->d_table);
         cudaFree(S->d_ctl);
         if (S->h_table) cudaFreeHost(S->h_table);
@@ -604,7 +627,7 @@ extern "C" bsgd_status bsgd_server_destroy(bsgd_server *S) {
     cudaStreamSynchronize(S->round_stream);
     for (auto &kv : S->geo_cache) bsgd_geometry_destroy(kv.second.g);
     for (auto &kv : S->pinned_free) cudaFreeHost(kv.second);
-    if (S->graph) cudaGraphExecDestroy(S->graph);
+    for (auto &kv : S->graphs) cudaGraphExecDestroy(kv.second);
     cudaFree(S->d_table);
     cudaFree(S->d_ctl);
     cudaFreeHost(S->h_table);

@@ -9,6 +9,7 @@
 // column block, so they share the view's ray table entry and walk a compact
 // bundle of neighbouring voxels.
 #include <algorithm>
+#include <type_traits>
 
 #include "siddon_device.cuh"
 
@@ -489,18 +490,22 @@ __global__ void __launch_bounds__(256) nonzero_kernel(const T *__restrict__ x, i
     if (__syncthreads_or(nz) && threadIdx.x == 0) *flag = 1;
 }
 
-// z^j of block j at every view: grid x = tile of the view's band, y = views
-// (strided when there are more than gridDim.y).
+// z^j of every block at every view: work items (block, view, tile of the
+// view's band) taken in turn by a grid of a few CTAs per SM.
 template <bool k3D, typename T>
-__global__ void __launch_bounds__(128) warm_fp_kernel(const DeviceGeom G, int j,
+__global__ void __launch_bounds__(128) warm_fp_kernel(const DeviceGeom G, int tiles,
                                                       const T *__restrict__ x,
                                                       const T *__restrict__ xT, T *__restrict__ z,
                                                       const int *__restrict__ flag) {
     if (*flag == 0) return;
-    for (int a = blockIdx.y; a < G.n_views; a += gridDim.y) {
+    const int64_t total = (int64_t)G.N * G.n_views * tiles;
+    for (int64_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const int tile = (int)(item % tiles);
+        const int64_t ja = item / tiles;
+        const int a = (int)(ja % G.n_views), j = (int)(ja / G.n_views);
         const Band b = G.bands[(size_t)a * (G.N + 1) + j];
         int u, v, nt;
-        if (!tile_pixel<k3D>(b, blockIdx.x, u, v, nt)) continue;
+        if (!tile_pixel<k3D>(b, tile, u, v, nt)) continue;
         const bool yf = xT != nullptr && G.view_yfast[a];
         const T *src = yf ? xT : x;
         RayWalk w;
@@ -545,67 +550,91 @@ __global__ void __launch_bounds__(256) warm_residual_kernel(const DeviceGeom G,
 // Items are handed out by an atomic counter, so requests of very different
 // sizes share the GPU without a per-request launch.
 
-__device__ __forceinline__ int round_entry(const ReqDesc *T, int n, long long item) {
-    int r = 0;
-    while (r + 1 < n && T[r + 1].work_begin <= item) ++r;
+__device__ __forceinline__ int round_entry(const ReqDesc *T, int lo, int hi, long long item) {
+    int r = lo;
+    while (r + 1 < hi && T[r + 1].work_begin <= item) ++r;
     return r;
 }
 
-__global__ void __launch_bounds__(128) round_solve_kernel(const ReqDesc *__restrict__ T,
+// Persistent kernel of one class of requests (MULTI: several column blocks
+// per iteration; T: storage type): CTA-sized work items (one detector tile of
+// one view of one pair, or of one drawn row block with several column blocks)
+// handed out by the class's atomic counter. The request's geometry and solver
+// pointers are copied into shared memory when the CTA moves to another request,
+// so that the passes read them from there (as the plain kernels read their
+// parameters) instead of from the table in global memory, where they would
+// compete with the gathers for L1.
+template <bool MULTI, typename T>
+__global__ void __launch_bounds__(128, MULTI ? 7 : 10) round_solve_kernel(const ReqDesc *__restrict__ T_,
                                                           RoundCtl *__restrict__ C) {
+    constexpr int CLS = 3 * (MULTI ? 1 : 0) + (sizeof(T) == 4 ? BSGD_F32
+                                               : std::is_same<T, __nv_bfloat16>::value ? BSGD_BF16
+                                                                                       : BSGD_F16);
     __shared__ long long s_item;
+    __shared__ DeviceGeom sG;
+    __shared__ SolveDev sS;
+    static_assert(sizeof(DeviceGeom) % 4 == 0 && sizeof(SolveDev) % 4 == 0, "word copies");
+    const int lo = C->lo[CLS], hi = C->hi[CLS];
+    int cur = -1;
     for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&C->next, 1ull);
-        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&C->next[CLS], 1ull);
+        __syncthreads();   // the previous item is done with sG / sS; s_item is visible
         const long long item = s_item;
-        __syncthreads();
-        if (item >= C->total_items) return;
-        const ReqDesc &q = T[round_entry(T, C->n, item)];
-        if (!q.active || item >= q.work_begin + q.work_count) continue;
-        long long local = item - q.work_begin;
-        const int slot = (int)(local % q.G.max_views);
-        local /= q.G.max_views;
-        const int tile = (int)(local % q.max_tiles);
-        const int p = (int)(local / q.max_tiles);   // pair (one block) or row-block slot
-        if (q.kN == 1) {
-            if (q.dtype == BSGD_F32)
-                fpbp_solve_body<float>(q.G, q.S, (const float *)q.x, tile, slot, p);
-            else if (q.dtype == BSGD_BF16)
-                fpbp_solve_body<__nv_bfloat16>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
-            else
-                fpbp_solve_body<__half>(q.G, q.S, (const __half *)q.x, tile, slot, p);
-        } else if (q.kN <= 2) {
-            if (q.dtype == BSGD_F32)
-                fpbpm_solve_body<float, 2>(q.G, q.S, (const float *)q.x, tile, slot, p);
-            else if (q.dtype == BSGD_BF16)
-                fpbpm_solve_body<__nv_bfloat16, 2>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
-            else
-                fpbpm_solve_body<__half, 2>(q.G, q.S, (const __half *)q.x, tile, slot, p);
-        } else {
-            if (q.dtype == BSGD_F32)
-                fpbpm_solve_body<float, 4>(q.G, q.S, (const float *)q.x, tile, slot, p);
-            else if (q.dtype == BSGD_BF16)
-                fpbpm_solve_body<__nv_bfloat16, 4>(q.G, q.S, (const __nv_bfloat16 *)q.x, tile, slot, p);
-            else
-                fpbpm_solve_body<__half, 4>(q.G, q.S, (const __half *)q.x, tile, slot, p);
+        if (item >= C->total_items[CLS] || lo >= hi) return;
+        const int e = round_entry(T_, lo, hi, item);
+        const ReqDesc &q = T_[e];
+        if (e != cur) {
+            const uint32_t *gsrc = reinterpret_cast<const uint32_t *>(&q.G);
+            const uint32_t *ssrc = reinterpret_cast<const uint32_t *>(&q.S);
+            uint32_t *gdst = reinterpret_cast<uint32_t *>(&sG), *sdst = reinterpret_cast<uint32_t *>(&sS);
+            for (int k = threadIdx.x; k < (int)(sizeof(DeviceGeom) / 4); k += blockDim.x) gdst[k] = gsrc[k];
+            for (int k = threadIdx.x; k < (int)(sizeof(SolveDev) / 4); k += blockDim.x) sdst[k] = ssrc[k];
+            cur = e;
         }
+        const int active = q.active, max_tiles = q.max_tiles, kN = q.kN;
+        const int64_t wb = q.work_begin, wc = q.work_count;
+        const T *x = reinterpret_cast<const T *>(q.x);
+        __syncthreads();   // sG / sS are complete; every thread has read s_item
+        if (!active || item >= wb + wc) continue;
+        long long local = item - wb;
+        const int slot = (int)(local % sG.max_views);
+        local /= sG.max_views;
+        const int tile = (int)(local % max_tiles);
+        const int p = (int)(local / max_tiles);   // pair (one block) or row-block slot
+        if (!MULTI) fpbp_solve_body<T>(sG, sS, x, tile, slot, p);
+        else if (kN <= 2) fpbpm_solve_body<T, 2>(sG, sS, x, tile, slot, p);
+        else fpbpm_solve_body<T, 4>(sG, sS, x, tile, slot, p);
     }
 }
 
-int round_persistent_grid() {
-    int dev = 0, sms = 152, per = 4;
+namespace {
+template <bool MULTI, typename T>
+const void *round_kernel_ptr() { return (const void *)round_solve_kernel<MULTI, T>; }
+const void *round_kernel(int cls) {
+    switch (cls) {
+    case 0: return round_kernel_ptr<false, float>();
+    case 1: return round_kernel_ptr<false, __nv_bfloat16>();
+    case 2: return round_kernel_ptr<false, __half>();
+    case 3: return round_kernel_ptr<true, float>();
+    case 4: return round_kernel_ptr<true, __nv_bfloat16>();
+    default: return round_kernel_ptr<true, __half>();
+    }
+}
+}  // namespace
+
+int round_persistent_grid(int cls) {
+    int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int a = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, round_solve_kernel, 128, 0);
-    per = std::max(1, a);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, round_kernel(cls), 128, 0);
     cudaGetLastError();
-    return sms * per;
+    return sms * std::max(1, a);
 }
 
-bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int grid, cudaStream_t st) {
-    round_solve_kernel<<<grid, 128, 0, st>>>(table, ctl);
-    BSGD_CUDA(cudaGetLastError());
+bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int cls, int grid, cudaStream_t st) {
+    void *args[] = {(void *)&table, (void *)&ctl};
+    BSGD_CUDA(cudaLaunchKernel(round_kernel(cls), dim3(grid), dim3(128), args, 0, st));
     return BSGD_OK;
 }
 
@@ -838,18 +867,18 @@ bsgd_status launch_warm_start(const bsgd_geometry *g, const SolveDev &S, const v
     const int gr = (int)std::max<int64_t>(1, std::min<int64_t>((R + 255) / 256, 152 * 8));
     std::vector<int> all(g->desc.n_views);
     for (int a = 0; a < g->desc.n_views; ++a) all[a] = a;
+    int tiles = 0;   // the most tiles any (view, block) band needs
+    for (int j = 0; j < g->N; ++j) tiles = std::max(tiles, tiles_for(g, all, j, j + 1, tile_u(g), tile_v(g)));
+    const int gw = 152 * 8;
     const bool t3 = g->desc.nv > 1;
 #define WARM_GO(T)                                                                                 \
     {                                                                                              \
         nonzero_kernel<T><<<gn, 256, 0, st>>>((const T *)x, C, flag);                             \
-        for (int j = 0; j < g->N; ++j) {                                                           \
-            const int tiles = tiles_for(g, all, j, j + 1, tile_u(g), tile_v(g));                   \
-            if (tiles == 0) continue;                                                              \
-            dim3 grid(tiles, std::min(g->desc.n_views, 65535));                                    \
-            if (t3) warm_fp_kernel<true, T><<<grid, 128, 0, st>>>(g->dg, j, (const T *)x,          \
-                                                                  (const T *)S.xT, (T *)S.z, flag);\
-            else warm_fp_kernel<false, T><<<grid, 128, 0, st>>>(g->dg, j, (const T *)x,            \
+        if (tiles > 0) {                                                                           \
+            if (t3) warm_fp_kernel<true, T><<<gw, 128, 0, st>>>(g->dg, tiles, (const T *)x,        \
                                                                 (const T *)S.xT, (T *)S.z, flag);  \
+            else warm_fp_kernel<false, T><<<gw, 128, 0, st>>>(g->dg, tiles, (const T *)x,          \
+                                                              (const T *)S.xT, (T *)S.z, flag);    \
         }                                                                                          \
         warm_residual_kernel<T><<<gr, 256, 0, st>>>(g->dg, (const T *)S.y, (const T *)S.z,         \
                                                     (T *)S.r, flag);                               \

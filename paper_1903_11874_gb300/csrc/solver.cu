@@ -838,6 +838,7 @@ struct bsgd_state {
     int64_t *d_iter = nullptr;
     int *x0_flag = nullptr;     // warm start: 1 if the starting image is not zero
     unsigned char *owned = nullptr;  // owner-computes sharding: owned column blocks (N)
+    bool zero_start = false;    // the caller's image is known to be zero: no warm start
     int32_t *trace = nullptr, *replay = nullptr;
     int64_t replay_start = 0, replay_n = 0;
     unsigned long long *counts = nullptr, *updates = nullptr;
@@ -1277,8 +1278,18 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         if (p->step_rule == BSGD_STEP_FIXED) {
             s->mu = p->mu;
         } else {
+            const std::pair<int, int> key(p->step_rule, p->power_iters);
             double lmax = 0.0;
-            for (int j = 0; j < N; ++j) {
+            bool cached = false;
+            {
+                std::lock_guard<std::mutex> lock(g->cache_mu);
+                auto it = g->lambda_cache.find(key);
+                if (it != g->lambda_cache.end()) {
+                    lmax = it->second;
+                    cached = true;
+                }
+            }
+            for (int j = 0; j < N && !cached; ++j) {
                 if (p->step_rule == BSGD_STEP_STRIP) {
                     double lam = 0.0;
                     BSGD_TRY(power_iteration(g, j, p->power_iters, nullptr, 0, &lam, st));
@@ -1292,6 +1303,10 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
                 }
             }
             if (!(lmax > 0)) return fail(BSGD_ERR_INVALID_ARG, "A^J is zero for every block");
+            {
+                std::lock_guard<std::mutex> lock(g->cache_mu);
+                g->lambda_cache.emplace(key, lmax);
+            }
             s->mu = p->rho / lmax;
         }
         BSGD_CUDA(cudaMemcpyAsync(s->d_mu, &s->mu, 8, cudaMemcpyHostToDevice, st));
@@ -1501,7 +1516,9 @@ static bsgd_status launch_update(bsgd_state *s, void *x, cudaStream_t st, bool d
     const int64_t nt = s->gT ? ((g->desc.nx + 31) / 32) * (int64_t)((g->desc.ny + 31) / 32) *
                                    ((maxJ + (int64_t)g->desc.nx * g->desc.ny - 1) / ((int64_t)g->desc.nx * g->desc.ny))
                              : (maxJ + 1023) / 1024;
-    dim3 ug((unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, 65535)), s->kN);
+    // a grid of 4 CTAs per SM walks the tiles (the update is short: a second,
+    // partial wave of one CTA per tile cost more than the loop)
+    dim3 ug((unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, 152 * 4)), s->kN);
     if (draw_next) {
         // the draw of iteration k + 1 needs only the residual table, final
         // once this iteration's FPs are done: one extra CTA of the update
@@ -1619,7 +1636,7 @@ extern "C" bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void
     cudaStream_t st = (cudaStream_t)stream;
     if (s->owned) return fail(BSGD_ERR_STATE, "a sharded state steps through bsgd_shard_begin / _end");
     if (n_iters > 0) BSGD_TRY(sync_xT(s, x, st));
-    if (n_iters > 0 && s->iters == 0) BSGD_TRY(warm_start(s, x, st));
+    if (n_iters > 0 && s->iters == 0 && !s->zero_start) BSGD_TRY(warm_start(s, x, st));
     for (int k = 0; k < n_iters; ++k) BSGD_TRY(one_iteration(s, x, st, k > 0, k + 1 < n_iters));
     return BSGD_OK;
 }
@@ -1999,6 +2016,7 @@ extern "C" bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_param
         if (xh) BSGD_TRY(palloc(&dx, C * dtype_size(xt), st));
         if (p->zero_start) {
             BSGD_CUDA(cudaMemsetAsync(xs, 0, C * dtype_size(sd), st));
+            s->zero_start = true;   // the state already describes x0 = 0
         } else {
             const void *x0 = x;
             if (xh) {

@@ -256,6 +256,10 @@ def test_block_step_rule_matches_oracle():
     st = B.State(gg, prm, torch.zeros(gg.n_rows, device=DEV))
     mu = RHO / lam.max()
     assert abs(st.query()["mu"] - mu) <= 1e-5 * mu
+    # the estimate is kept with the geometry: a second state takes the same mu
+    st2 = B.State(gg, B.SolveParams(**{**prm.__dict__, "rho": 2 * RHO}),
+                  torch.zeros(gg.n_rows, device=DEV))
+    assert st2.query()["mu"] == 2 * st.query()["mu"]
     # a row block sees part of the strip: its norm is below the strip's
     strip = max(OB.power_iteration(og, N, j, 20) for j in range(N))
     assert lam.max() < strip
