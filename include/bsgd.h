@@ -17,6 +17,8 @@
  *    host pointers and copies them itself.
  *  - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls are
  *    asynchronous on that stream unless their comment says they synchronise.
+ *  - Kernels run on the calling thread's current CUDA device, which must be
+ *    the device the geometry was created on (INVALID_ARG otherwise).
  *  - Volumes are stored [z][y][x] (x fastest), sinograms [view][v][u]
  *    (u fastest). Element types are given by bsgd_dtype.
  *  - The library owns the geometry tables and the solver state behind the
@@ -192,9 +194,14 @@ bsgd_status bsgd_count_updates(const bsgd_geometry *g,
  *  - Geometries with more than 16384 views are rejected (INVALID_ARG).
  *  - Calls no cudaMalloc / cudaFree and no allocating library routine.
  *  - The first call on a device looks up the array's device address (once per
- *    device); make that first call before any stream capture.
+ *    device) and keeps it for the process's life (a cudaDeviceReset makes it
+ *    stale: do not call this entry point again after one).
+ *  - Synchronous (it reads the total back into *out): do not call it on a
+ *    stream that is being captured into a CUDA graph.
  *  - Every call on a device shares the array (each call clears it first);
  *    calls that overlap on the GPU race and give wrong counts.
+ *  - Host side it uses about 4 KiB of the calling thread's stack and no heap.
+ *  - INVALID_ARG when the current device is not the geometry's device.
  */
 bsgd_status bsgd_count_updates_noalloc(const bsgd_geometry *g,
                                        const int32_t *row_blocks, int n_rb,

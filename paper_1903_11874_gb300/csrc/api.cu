@@ -18,6 +18,7 @@ bsgd_status block_lists(const bsgd_geometry *g, const int32_t *row_blocks, int n
                         std::vector<std::pair<int, int>> &runs) {
     rows.clear();
     runs.clear();
+    BSGD_TRY(check_device(g));
     if (row_blocks) {
         if (n_rb < 1) return fail(BSGD_ERR_INVALID_ARG, "n_rb must be >= 1");
         std::set<int> seen;

@@ -20,6 +20,9 @@ namespace bsgd {
 
 void set_error(const std::string &msg);
 bsgd_status fail(bsgd_status s, const std::string &msg);
+// INVALID_ARG unless the calling thread's current CUDA device holds g's tables
+// (every launch runs on the current device).
+bsgd_status check_device(const bsgd_geometry *g);
 bsgd_status cuda_fail(cudaError_t e, const char *what);
 
 #define BSGD_CUDA(call)                                                    \

@@ -108,34 +108,37 @@ extern "C" bsgd_status bsgd_count_updates_noalloc(const bsgd_geometry *g, const 
         return fail(BSGD_ERR_INVALID_ARG,
                     "bsgd_count_updates_noalloc supports at most 16384 views (its counters are a "
                     "fixed array); use bsgd_count_updates");
-    // selected row blocks (stack only: this entry point allocates nothing)
-    int rows[kNoAllocMaxViews];
-    int nr = 0;
-    bool seen_r[kNoAllocMaxViews] = {};
+    if (g->N > kNoAllocMaxViews) return fail(BSGD_ERR_INVALID_ARG, "too many column blocks");
+    // the kernels run on the current device: it must be the one holding the
+    // geometry's tables
+    BSGD_TRY(check_device(g));
+    // selected blocks as bit sets on the stack (4 KiB in all: this entry point
+    // allocates nothing, on the device or on the host)
+    constexpr int kWords = kNoAllocMaxViews / 32;
+    uint32_t seen_r[kWords] = {}, cols[kWords] = {};
+    auto has = [](const uint32_t *set, int k) { return (set[k >> 5] >> (k & 31)) & 1u; };
+    auto put = [](uint32_t *set, int k) { set[k >> 5] |= 1u << (k & 31); };
+    int nr = g->M;
     if (row_blocks) {
         if (n_rb < 1) return fail(BSGD_ERR_INVALID_ARG, "n_rb must be >= 1");
         for (int k = 0; k < n_rb; ++k) {
             const int i = row_blocks[k];
             if (i < 0 || i >= g->M) return fail(BSGD_ERR_INVALID_ARG, "row block id out of range");
-            if (seen_r[i]) return fail(BSGD_ERR_INVALID_ARG, "duplicate row block id");
-            seen_r[i] = true;
-            rows[nr++] = i;
+            if (has(seen_r, i)) return fail(BSGD_ERR_INVALID_ARG, "duplicate row block id");
+            put(seen_r, i);
         }
-    } else {
-        for (int i = 0; i < g->M; ++i) rows[nr++] = i;
+        nr = n_rb;
     }
-    bool cols[kNoAllocMaxViews] = {};
-    if (g->N > kNoAllocMaxViews) return fail(BSGD_ERR_INVALID_ARG, "too many column blocks");
     if (col_blocks) {
         if (n_cb < 1) return fail(BSGD_ERR_INVALID_ARG, "n_cb must be >= 1");
         for (int k = 0; k < n_cb; ++k) {
             const int j = col_blocks[k];
             if (j < 0 || j >= g->N) return fail(BSGD_ERR_INVALID_ARG, "column block id out of range");
-            if (cols[j]) return fail(BSGD_ERR_INVALID_ARG, "duplicate column block id");
-            cols[j] = true;
+            if (has(cols, j)) return fail(BSGD_ERR_INVALID_ARG, "duplicate column block id");
+            put(cols, j);
         }
     } else {
-        for (int j = 0; j < g->N; ++j) cols[j] = true;
+        for (int j = 0; j < g->N; ++j) put(cols, j);
     }
     unsigned long long *counts = nullptr;
     BSGD_TRY(counter_address(&counts));
@@ -144,15 +147,15 @@ extern "C" bsgd_status bsgd_count_updates_noalloc(const bsgd_geometry *g, const 
     const bool t3 = g->desc.nv > 1;
     const int tu = tile_u(g), tv = tile_v(g);
     for (int j0 = 0; j0 < g->N;) {
-        if (!cols[j0]) { ++j0; continue; }
+        if (!has(cols, j0)) { ++j0; continue; }
         int j1 = j0 + 1;
-        while (j1 < g->N && cols[j1]) ++j1;
+        while (j1 < g->N && has(cols, j1)) ++j1;
         for (int k0 = 0; k0 < nr; k0 += 64) {
             NoAllocRows R{};
             R.n = nr - k0 < 64 ? nr - k0 : 64;
             int tiles = 0;
             for (int k = 0; k < R.n; ++k) {
-                R.ids[k] = rows[k0 + k];
+                R.ids[k] = row_blocks ? row_blocks[k0 + k] : k0 + k;
                 for (int a : g->block_views[R.ids[k]]) {
                     Band b{1 << 30, -1, 1 << 30, -1};
                     if (j0 == 0 && j1 == g->N) {

@@ -25,6 +25,19 @@ bsgd_status fail(bsgd_status s, const std::string &msg) {
     return s;
 }
 
+bsgd_status check_device(const bsgd_geometry *g) {
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BSGD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    }
+    if (dev != g->device)
+        return fail(BSGD_ERR_INVALID_ARG, "the current CUDA device (" + std::to_string(dev) +
+                                              ") is not the geometry's (" + std::to_string(g->device) + ")");
+    return BSGD_OK;
+}
+
 bsgd_status cuda_fail(cudaError_t e, const char *what) {
     set_error(std::string(what) + ": " + cudaGetErrorString(e));
     return BSGD_ERR_CUDA;

@@ -1090,6 +1090,7 @@ extern "C" bsgd_status bsgd_power_iteration(const bsgd_geometry *g, int col_bloc
     if (!g || !lambda_out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
     if (col_block < 0 || col_block >= g->N) return fail(BSGD_ERR_INVALID_ARG, "col_block out of range");
     if (iters < 0) return fail(BSGD_ERR_INVALID_ARG, "iters < 0");
+    BSGD_TRY(check_device(g));
     if (row_blocks)
         for (int k = 0; k < n_rb; ++k)
             if (row_blocks[k] < 0 || row_blocks[k] >= g->M)
@@ -1206,6 +1207,7 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
     *out = nullptr;
     if (!dtype_ok(yt)) return fail(BSGD_ERR_INVALID_ARG, "bad y dtype");
     BSGD_TRY(check_params(g, p));
+    BSGD_TRY(check_device(g));
     cudaStream_t st = (cudaStream_t)stream;
     bsgd_state *s = new (std::nothrow) bsgd_state();
     if (!s) return fail(BSGD_ERR_OOM, "host allocation failed");
@@ -1633,6 +1635,7 @@ static bsgd_status warm_start(bsgd_state *s, void *x, cudaStream_t st) {
 extern "C" bsgd_status bsgd_block_step(bsgd_state *s, void *x, int n_iters, void *stream) {
     if (!s || !x) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
     if (n_iters < 0) return fail(BSGD_ERR_INVALID_ARG, "n_iters < 0");
+    BSGD_TRY(check_device(s->g));
     cudaStream_t st = (cudaStream_t)stream;
     if (s->owned) return fail(BSGD_ERR_STATE, "a sharded state steps through bsgd_shard_begin / _end");
     if (n_iters > 0) BSGD_TRY(sync_xT(s, x, st));
@@ -1702,6 +1705,7 @@ extern "C" bsgd_status bsgd_state_set_shard(bsgd_state *s, const int32_t *owned_
 extern "C" bsgd_status bsgd_shard_begin(bsgd_state *s, void *x, float *exchange, void *stream) {
     if (!s || !x || !exchange) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
     if (!s->owned) return fail(BSGD_ERR_STATE, "not a sharded state (bsgd_state_set_shard)");
+    BSGD_TRY(check_device(s->g));
     const bsgd_geometry *g = s->g;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t k = s->iters;
@@ -1987,6 +1991,7 @@ extern "C" bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_param
                                   bsgd_report *out, void *stream) {
     if (!g || !p || !y || !x) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
     if (!dtype_ok(yt) || !dtype_ok(xt)) return fail(BSGD_ERR_INVALID_ARG, "bad dtype");
+    BSGD_TRY(check_device(g));
     cudaStream_t st = (cudaStream_t)stream;
     auto on_host = [](const void *ptr) {
         cudaPointerAttributes at{};

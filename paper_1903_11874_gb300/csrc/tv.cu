@@ -165,6 +165,7 @@ extern "C" bsgd_status bsgd_tv_prox(const bsgd_geometry *g, void *x, bsgd_dtype 
     if (!dtype_ok(xt)) return fail(BSGD_ERR_INVALID_ARG, "bad dtype");
     if (!(kappa >= 0) || iters < 0) return fail(BSGD_ERR_INVALID_ARG, "kappa >= 0, iters >= 0");
     if (g->desc.nz > 65535) return fail(BSGD_ERR_INVALID_ARG, "TV prox supports nz <= 65535");
+    BSGD_TRY(check_device(g));
     if (!(kappa > 0) || iters < 1) return BSGD_OK;
     cudaStream_t st = (cudaStream_t)stream;
     TvWork w;
