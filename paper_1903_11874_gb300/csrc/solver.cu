@@ -64,7 +64,23 @@ constexpr int kSampleSmemS = 2048;     // residual-table entries staged in share
 // cells), executed by one CTA of kSampleThreads threads. Writes the work list,
 // the chosen cells, the trace entry and the update counter, then advances the
 // iteration counter.
-__device__ void sample_body(const SampleArgs &A) {
+// Residual-pair weights W_k = sum over the pair's detector rows of S[i][v] for
+// the pairs k0 <= k < k1, one warp per pair (lanes over rows in a fixed order,
+// then a fixed shuffle tree): the same sums whichever CTA computes them.
+__device__ void pair_weights(const SampleArgs &A, const double *S, int k0, int k1, double *out) {
+    const DeviceGeom &G = A.G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int k = k0 + warp; k < k1; k += nwarps) {
+        const int lo = A.wband[2 * k], hi = A.wband[2 * k + 1];
+        const int i = k / G.N;
+        double w = 0.0;
+        for (int v = lo + lane; v <= hi; v += 32) w += S[(size_t)i * G.nv + v];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) out[k] = w;
+    }
+}
+
+__device__ void sample_body(const SampleArgs &A, const double *pre_w = nullptr) {
     // one buffer, two uses: the uniform draw's permutations, or the residual
     // table (staged with one parallel load: the draw is a latency chain) and
     // the pair weights
@@ -121,6 +137,46 @@ __device__ void sample_body(const SampleArgs &A) {
                     ++np;
                 }
             s_np = np;
+        }
+    } else if (pre_w) {  // residual-weighted pair, weights computed by other CTAs
+        const int MN = G.M * G.N;
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int k = tid; k < MN; k += blockDim.x) s_w[k] = __ldcg(pre_w + k);
+        __syncthreads();
+        if (warp == 0) {
+            double t = 0.0;
+            for (int k = lane; k < MN; k += 32) t += s_w[k];
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            const double fl = kResidualFloor * t / MN + 1e-300;
+            double carry = 0.0;
+            for (int b = 0; b < MN; b += 32) {
+                double v = b + lane < MN ? s_w[b + lane] + fl : 0.0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double n = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += n;
+                }
+                carry += __shfl_sync(0xffffffffu, v, 31);
+            }
+            const double c = draw_u(A.seed, it, kLanePair) * carry;
+            int pick = -1;
+            carry = 0.0;
+            for (int b = 0; b < MN && pick < 0; b += 32) {
+                double v = b + lane < MN ? s_w[b + lane] + fl : 0.0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double n = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += n;
+                }
+                v += carry;
+                const unsigned hit = __ballot_sync(0xffffffffu, b + lane < MN && v > c);
+                if (hit) pick = b + __ffs(hit) - 1;
+                carry = __shfl_sync(0xffffffffu, v, 31);
+            }
+            if (pick < 0) pick = MN - 1;
+            if (lane == 0) {
+                s_np = 1;
+                s_pi[0] = pick / G.N;
+                s_pj[0] = pick % G.N;
+            }
         }
     } else {  // residual-weighted pair: W_ij = sum_{v in R_ij} S[i][v] + floor
         const int MN = G.M * G.N;
@@ -530,18 +586,38 @@ __device__ void update_body(const DeviceGeom &G, const SolveDev &S, T *__restric
     }
 }
 
-// The block update of this iteration (CTAs x >= 1 of each row) and the draw
-// of the next iteration (CTA (0, 0), the first one dispatched, so that the
-// one-CTA draw runs beside the update instead of after it).
+// The block update of this iteration and the draw of the next (the first
+// `dc` CTAs of row 0, dispatched first, so that the draw runs beside the
+// update instead of after it). With dc > 1 (residual-weighted pairs) the draw
+// CTAs split the pair weights between them and the last one to finish (an
+// atomic ticket) takes the draw: the FP64 sums are spread over dc SMs.
 template <typename T>
 __global__ void __launch_bounds__(256) update_sample_kernel(const DeviceGeom G, const SolveDev S,
                                                             T *__restrict__ x, T *__restrict__ xlo,
-                                                            const SampleArgs An) {
-    if (blockIdx.x == 0) {
-        if (blockIdx.y == 0) sample_body(An);
+                                                            const SampleArgs An, int dc,
+                                                            double *wscratch, unsigned *ticket) {
+    if ((int)blockIdx.x < dc) {
+        if (blockIdx.y != 0) return;
+        if (dc == 1) {
+            sample_body(An);
+            return;
+        }
+        const int MN = G.M * G.N;
+        const int per = (MN + dc - 1) / dc;
+        const int k0 = min(MN, (int)blockIdx.x * per), k1 = min(MN, k0 + per);
+        pair_weights(An, An.S, k0, k1, wscratch);
+        __threadfence();
+        __syncthreads();
+        __shared__ unsigned s_last;
+        if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == (unsigned)dc - 1;
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        sample_body(An, wscratch);
+        if (threadIdx.x == 0) *ticket = 0u;
         return;
     }
-    update_body<T>(G, S, x, xlo, blockIdx.y, blockIdx.x - 1, gridDim.x - 1);
+    update_body<T>(G, S, x, xlo, blockIdx.y, blockIdx.x - dc, gridDim.x - dc);
 }
 
 // xT = transpose(x) over the whole volume (y fastest), through shared memory.
@@ -837,6 +913,8 @@ struct bsgd_state {
     int *cells = nullptr, *wband = nullptr;
     int64_t *d_iter = nullptr;
     int *x0_flag = nullptr;     // warm start: 1 if the starting image is not zero
+    double *wscratch = nullptr; // residual-pair weights of a split draw
+    unsigned *ticket = nullptr; // the split draw's completion counter
     unsigned char *owned = nullptr;  // owner-computes sharding: owned column blocks (N)
     bool zero_start = false;    // the caller's image is known to be zero: no warm start
     int32_t *trace = nullptr, *replay = nullptr;
@@ -959,8 +1037,8 @@ static void free_state(bsgd_state *s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     // counts and cw belong to the geometry's cache; replay is a plain allocation
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->x0_flag, s->owned, s->trace, s->updates, s->pair_upd,
-                    s->eud, s->eud_prev, s->am_part, s->am};
+                    s->wband, s->d_iter, s->x0_flag, s->owned, s->wscratch, s->ticket, s->trace,
+                    s->updates, s->pair_upd, s->eud, s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) pfree(p);
     cudaFree(s->replay);
     tv_work_free(s->tv);
@@ -1242,6 +1320,8 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         (e = palloc((void **)&s->cells, 2 * 4 * (size_t)kMaxPairs * g->max_views, st)) ||
         (e = palloc((void **)&s->wband, 4 * g->wband.size(), st)) ||
         (e = palloc((void **)&s->d_iter, 8, st)) || (e = palloc((void **)&s->x0_flag, 8, st)) ||
+        (e = palloc((void **)&s->wscratch, 8 * (size_t)kMaxResidualPairs, st)) ||
+        (e = palloc((void **)&s->ticket, 8, st)) ||
         (e = palloc((void **)&s->trace, 4 * (size_t)s->trace_cap * s->stride, st)) ||
         (e = palloc((void **)&s->updates, 8, st)) ||
         (e = palloc((void **)&s->pair_upd, 8 * (size_t)M * N, st)) ||
@@ -1267,6 +1347,7 @@ extern "C" bsgd_status bsgd_state_create(const bsgd_geometry *g, const bsgd_solv
         if (s->xT) BSGD_CUDA(cudaMemsetAsync(s->xT, 0, C * es, st));
         if (s->gT) BSGD_CUDA(cudaMemsetAsync(s->gT, 0, C * 4, st));
         BSGD_CUDA(cudaMemsetAsync(s->d_iter, 0, 8, st));
+        BSGD_CUDA(cudaMemsetAsync(s->ticket, 0, 8, st));
         BSGD_CUDA(cudaMemsetAsync(s->updates, 0, 8, st));
         BSGD_CUDA(cudaMemsetAsync(s->work, 0, 2 * sizeof(Work), st));
         BSGD_CUDA(cudaMemsetAsync(s->cells, 0xff, 2 * 4 * (size_t)kMaxPairs * g->max_views, st));
@@ -1367,8 +1448,8 @@ void state_release(bsgd_state *s, cudaStream_t st) {
     }
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     void *ptrs[] = {s->y, s->z, s->rt, s->r, s->xlo, s->xT, s->gT, s->grad, s->S, s->d_mu, s->work, s->cells,
-                    s->wband, s->d_iter, s->x0_flag, s->owned, s->trace, s->updates, s->pair_upd,
-                    s->eud, s->eud_prev, s->am_part, s->am};
+                    s->wband, s->d_iter, s->x0_flag, s->owned, s->wscratch, s->ticket, s->trace,
+                    s->updates, s->pair_upd, s->eud, s->eud_prev, s->am_part, s->am};
     for (void *p : ptrs) pool_free(p, st);
     delete s;
 }
@@ -1526,13 +1607,21 @@ static bsgd_status launch_update(bsgd_state *s, void *x, cudaStream_t st, bool d
         // once this iteration's FPs are done: one extra CTA of the update
         SampleArgs An;
         fill_sample_args(s, An, k + 1);
-        dim3 ugs(ug.x + 1, ug.y);
+        // residual-weighted pairs (not replayed): the weights split over 8 CTAs
+        const bool replay_next = s->replay && k + 1 >= s->replay_start && k + 1 < s->replay_start + s->replay_n;
+        const int dc = (s->p.pair_sampling == BSGD_PAIRS_RESIDUAL && !replay_next &&
+                        g->M * g->N >= 16) ? 8 : 1;
+        dim3 ugs(ug.x + dc, ug.y);
         if (s->st == BSGD_F32)
-            update_sample_kernel<float><<<ugs, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr, An);
+            update_sample_kernel<float><<<ugs, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr, An, dc,
+                                                             s->wscratch, s->ticket);
         else if (s->st == BSGD_BF16)
-            update_sample_kernel<__nv_bfloat16><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo, An);
+            update_sample_kernel<__nv_bfloat16><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x,
+                                                                     (__nv_bfloat16 *)s->xlo, An, dc,
+                                                                     s->wscratch, s->ticket);
         else
-            update_sample_kernel<__half><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo, An);
+            update_sample_kernel<__half><<<ugs, 256, 0, st>>>(g->dg, s->dev, (__half *)x, (__half *)s->xlo,
+                                                              An, dc, s->wscratch, s->ticket);
     } else {
         if (s->st == BSGD_F32) update_kernel<float><<<ug, 256, 0, st>>>(g->dg, s->dev, (float *)x, nullptr);
         else if (s->st == BSGD_BF16) update_kernel<__nv_bfloat16><<<ug, 256, 0, st>>>(g->dg, s->dev, (__nv_bfloat16 *)x, (__nv_bfloat16 *)s->xlo);
