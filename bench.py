@@ -109,7 +109,16 @@ def parse():
                     help="paper-scale cases to time (comma list of case1, case2, case3, im; 'off')")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the BF16-storage, TV-prox and autograd legs")
+    ap.add_argument("--legs", default="all",
+                    help="extra legs to run (comma list of " + ",".join(LEGS) + "; 'all')")
     return ap.parse_args()
+
+
+LEGS = ("update", "power", "geometry", "bf16", "automu", "tv", "autograd", "precision", "full_solve")
+
+
+def leg_wanted(args, name):
+    return args.legs == "all" or name in args.legs.split(",")
 
 
 def dist_env():
@@ -336,14 +345,15 @@ def run_cuda(args):
                "api": "bsgd_solve (1 epoch per call from x0 = 0 (zero_start), pinned host y and x, fixed mu)"}
 
     full_solve = None
-    if not args.no_e2e and rank == 0 and world == 1:
+    if not args.no_e2e and rank == 0 and world == 1 and leg_wanted(args, "full_solve"):
         full_solve = full_solve_leg(B, torch, y_np)
 
     extra = None
     if not args.no_extra and rank == 0 and world == 1:
-        extra = extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks)
+        extra = extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks,
+                           lambda name: leg_wanted(args, name))
 
-    if extra is not None:
+    if extra is not None and leg_wanted(args, "precision"):
         extra["P_precision_config"] = precision_leg(B, torch, dev)
 
     paper = None
@@ -479,10 +489,36 @@ def epoch_rate(B, torch, dev, gg, y, prm, warm=2, epochs=3, profile=False):
     return upd / (ms * 1e-3) / 1e9, prof, ms / epochs
 
 
-def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks):
+def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks, want=lambda name: True):
     """Measurements of the other rows of the hot path: the block update and the
-    TV prox against the HBM roofline, BF16 storage, the autograd projector."""
+    TV prox against the HBM roofline, BF16 storage, the autograd projector
+    (`want(name)` selects the legs)."""
     hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {}
+    if want("update"):
+        out.update(update_leg(B, torch, dev, gg, y, mu, prof, hbm))
+    if want("power"):
+        out.update(power_leg(B, torch, gg))
+    if want("geometry"):
+        t0 = time.perf_counter()
+        g2 = B.Geometry(M=M, N=N, **GEOM)
+        out["a1_geometry_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+        g2.close()
+    if want("bf16"):
+        prm16 = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu,
+                              pair_sampling=B.PAIRS_RESIDUAL, storage=B.BF16, seed=1)
+        v16, _, ms16 = epoch_rate(B, torch, dev, gg, y, prm16)
+        out["P_bf16_storage"] = {"value": round(v16, 3), "unit": UNIT, "ms_per_epoch": round(ms16, 3)}
+    if want("automu"):
+        out.update(automu_leg(B, torch, dev, gg, y, mu))
+    if want("tv"):
+        out.update(tv_leg(B, torch, dev, gg, y, mu, hbm))
+    if want("autograd"):
+        out.update(autograd_leg(B, torch, dev))
+    return out
+
+
+def update_leg(B, torch, dev, gg, y, mu, prof, hbm):
     out = {}
     # a7 and a2/a3 on their own: one iteration per call, so every call runs a
     # standalone draw and a plain block update (in longer calls the update
@@ -508,9 +544,16 @@ def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks):
                         "bound": "hbm"}
     ms_s = p1["sample"]["ms"] / max(p1["sample"]["launches"], 1)
     ms_us = prof["update"]["ms"] / max(prof["update"]["launches"], 1)
-    out["a2_a3_sample"] = {"ms_per_launch": round(ms_s, 4), "bound": "latency (one CTA)",
+    out["a2_a3_sample"] = {"ms_per_launch": round(ms_s, 4),
+                           "bound": "latency (one CTA standalone; inside the update launch the "
+                                    "pair weights are split over 8 CTAs)",
                            "update_with_next_draw_ms": round(ms_us, 4)}
+    return out
+
+
+def power_leg(B, torch, gg):
     # a8: the step size's FP64 power iteration, 30 steps (FP + BP) of one strip
+    out = {}
     j = 0
     per_fp = B.bsgd_count_updates(gg, col_blocks=[j])
     B.bsgd_power_iteration(gg, j, 2)
@@ -521,16 +564,11 @@ def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks):
     out["a8_power_iteration"] = {"ms": round(dt * 1e3, 2), "iterations": 30,
                                  "value": round(2 * 30 * per_fp / dt / 1e9, 3), "unit": UNIT,
                                  "note": "one column strip, all views; FP64 vector state"}
-    # a1: geometry and band tables (host FP64, uploaded)
-    t0 = time.perf_counter()
-    g2 = B.Geometry(M=M, N=N, **GEOM)
-    out["a1_geometry_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
-    g2.close()
-    # P: the same workload with BF16 storage (FP32 arithmetic)
-    prm16 = B.SolveParams(alpha=1 / M, gamma=1 / N, step_rule=B.STEP_FIXED, mu=mu,
-                          pair_sampling=B.PAIRS_RESIDUAL, storage=B.BF16, seed=1)
-    v16, _, ms16 = epoch_rate(B, torch, dev, gg, y, prm16)
-    out["P_bf16_storage"] = {"value": round(v16, 3), "unit": UNIT, "ms_per_epoch": round(ms16, 3)}
+    return out
+
+
+def automu_leg(B, torch, dev, gg, y, mu):
+    out = {}
     # NEXT-1: Algorithm 3 on (a test at the end of every epoch: FP64 EUD
     # accumulation in the update, a reduction and the decision on the device)
     # against the same epochs with a fixed step
@@ -543,6 +581,11 @@ def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks):
     out["NEXT1_auto_mu"] = {"value": round(vam, 3), "unit": UNIT, "ms_per_epoch": round(msam, 3),
                             "fixed_step_value": round(v32, 3),
                             "overhead_pct": round(100.0 * (v32 / vam - 1.0), 2), "window_epochs": 1}
+    return out
+
+
+def tv_leg(B, torch, dev, gg, y, mu, hbm):
+    out = {}
     # a9: TV prox (FGP, 20 iterations) once per epoch; algorithmic bytes: 72 B
     # per voxel and FGP iteration (primal: b, r_xyz read, u written; dual: u,
     # r_xyz, p_xyz read, p_xyz, r_xyz written) + 80 B per voxel for the set-up
@@ -556,6 +599,11 @@ def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks):
                          "achieved_gbs": round(btv / (ms_tv * 1e-3) / 1e9, 1), "peak_gbs": hbm,
                          "frac": round(btv / (ms_tv * 1e-3) / 1e9 / hbm, 4), "bound": "hbm",
                          "fgp_iterations": 20}
+    return out
+
+
+def autograd_leg(B, torch, dev):
+    out = {}
     # D: Projector forward + backward on a batch
     from paper_1903_11874_gb300.autograd import Projector
     ga = B.Geometry(M=1, N=1, **AUTOGRAD_GEOM)
