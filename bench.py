@@ -51,8 +51,12 @@ ALU_OPS_PER_UPDATE = 5
 TRAFFIC_PER_LAUNCH = {"fpbp": 46_481_784}
 # What does bind the fused kernel, from the same kernel's ncu --set full capture
 # (the full capture summarised under profiles/, the heavier of two pairs):
-# L2 and L1/TEX throughput in % of their peaks, issue-active cycles in %.
-ON_CHIP_NCU = {"fpbp": {"l2_pct": 64.3, "l1tex_pct": 68.6, "issue_active_pct": 47.2}}
+# L2 and L1/TEX throughput in % of their peaks, issue-active cycles in %, and
+# L1 -> L2 sector operations per voxel-ray update (FP + BP) and per BP update
+# (the reductions).
+ON_CHIP_NCU = {"fpbp": {"l2_pct": 64.6, "l1tex_pct": 68.3, "issue_active_pct": 46.8,
+                        "l2_sectors_per_update": 0.30, "red_sectors_per_bp_update": 0.51,
+                        "thread_instructions_per_update": 23.7}}
 
 
 # Serving workload: Poisson arrivals (20 / s), request sizes n^3 with (256 / n) mm
