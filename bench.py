@@ -121,6 +121,13 @@ def parse():
 LEGS = ("update", "power", "geometry", "bf16", "automu", "tv", "autograd", "precision", "full_solve")
 
 
+def bench_config(world):
+    """The workload both arms run (the same dict on both, so that their lines
+    compare)."""
+    return {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def leg_wanted(args, name):
     return args.legs == "all" or name in args.legs.split(",")
 
@@ -380,16 +387,15 @@ def run_cuda(args):
             "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ellipsoid phantom, Poisson noise)",
-            "config": {"workload": WORKLOAD, "global_batch": world, "seq_len": None,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (state ~0.8 GB resident; one iteration "
+            "config": bench_config(world),
+            "method": {"l2": "inputs larger than L2 (state ~0.8 GB resident; one iteration "
                              "touches ~100 MB across launches of different slabs)",
                        "timing": "value over K epochs without per-stage events; roofline and "
                                  "stages_ms from K more epochs with a CUDA event pair around "
-                                 "every launch (ms_per_step_profiled)",
-                       "mu": mu, "residual_norm_end": q1["residual_norm"],
-                       "compact_rows_frac": round(gg.compact_rows / (N * gg.n_rows), 4),
-                       "state_gb": round(B.bsgd_request_bytes(GEOM, M, N, prm) / 1e9, 3)},
+                                 "every launch (ms_per_step_profiled)"},
+            "run": {"mu": mu, "residual_norm_end": q1["residual_norm"],
+                    "compact_rows_frac": round(gg.compact_rows / (N * gg.n_rows), 4),
+                    "state_gb": round(B.bsgd_request_bytes(GEOM, M, N, prm) / 1e9, 3)},
             "gpu_launches": int(launches), "stages_ms": stages,
             "ms_per_step_profiled": round(ms_profiled / args.steps, 3),
             "kernels": "split FP / BP" if args.split else "fused FP+residual+BP",
@@ -990,7 +996,9 @@ def run_reference(args):
         "ms_per_step": round(dt * 1e3 / args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded ellipsoid phantom, Poisson noise)",
-        "config": {"workload": WORKLOAD, "step": "1 BSGD block iteration per step (bounded sample)"},
+        "config": bench_config(world),
+        "method": {"step": "1 oracle BSGD block iteration per step (a bounded sample of the "
+                           "workload's epoch of 64 iterations)"},
         "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": OP.num_threads(),
                          "kind": "oracle",
                          "sample": "%d oracle BSGD iterations after %d warm-up" % (args.steps, args.warmup)},
