@@ -113,3 +113,38 @@ def test_two_processes_each_owning_half_the_blocks():
     ref = oracle_run(og, y, mu, False)
     for _, x, _ in res:
         assert rel_l2(x, ref.x) <= 1e-5
+
+
+def _nccl_one(port, out):
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import torch.distributed as dist
+    from paper_1903_11874_gb300 import binding as B
+    from paper_1903_11874_gb300 import shard
+    torch.cuda.set_device(0)
+    dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1)
+    try:
+        s, og, y, mu = setup()
+        gg = gpu_geom(s)
+        solver = shard.sharded_state(gg, gpu_params(B, mu, False), torch.from_numpy(y).cuda(), 0, 1)
+        assert solver.exchange.backend == "nccl"
+        x = torch.zeros(gg.n_cols, device="cuda:0")
+        solver.block_step(x, ITERS)
+        torch.cuda.synchronize()
+        out.put(x.cpu().numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_nccl_exchange_on_the_device():
+    """The exchange through NCCL (an in-place all-reduce of the device buffer),
+    one process owning every block: the same trajectory as the oracle."""
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_nccl_one, args=(_free_port(), q))
+    p.start()
+    x = q.get(timeout=600)
+    p.join(120)
+    assert p.exitcode == 0
+    _, og, y, mu = setup()
+    assert rel_l2(x, oracle_run(og, y, mu, False).x) <= 1e-5
