@@ -121,6 +121,7 @@ def _nccl_one(port, out):
     import torch.distributed as dist
     from paper_1903_11874_gb300 import binding as B
     from paper_1903_11874_gb300 import shard
+    os.environ.setdefault("NCCL_NVLS_ENABLE", "0")   # no NVLink multicast objects
     torch.cuda.set_device(0)
     dist.init_process_group("nccl", init_method="tcp://127.0.0.1:%d" % port, rank=0, world_size=1)
     try:
