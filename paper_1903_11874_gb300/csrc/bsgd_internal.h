@@ -360,9 +360,13 @@ bsgd_status convert(const void *in, bsgd_dtype it, void *out, bsgd_dtype ot, int
 // Round kernels of the server (enqueued once into a captured graph).
 bsgd_status launch_round_sample(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
                                 cudaStream_t st);
-bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int cls, int grid, cudaStream_t st);
+// ct: read the table from the device's constant copy (upload_round_const_table)
+bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int cls, bool ct, int grid,
+                               cudaStream_t st);
+constexpr int kRoundConstSlots = 64;   // entries of the constant-memory table (one server per device)
+bsgd_status upload_round_const_table(const ReqDesc *h, int n, cudaStream_t st);
 bsgd_status launch_round_update(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
                                 cudaStream_t st);
-int round_persistent_grid(int cls);
+int round_persistent_grid(int cls, bool ct);
 
 }  // namespace bsgd

@@ -110,6 +110,7 @@ struct bsgd_server {
     std::map<int, cudaGraphExec_t> graphs;   // round graph per set of classes present
     int class_mask = 0;                      // classes of the current table
     int grid[kRoundClasses] = {};   // persistent grid of each class's kernel
+    bool const_table = false;       // this server holds the device's constant request table
     // stats
     int64_t submitted = 0, admitted = 0, completed = 0, failed = 0, rounds = 0;
     int peak_resident = 0;
@@ -122,6 +123,24 @@ struct bsgd_server {
 namespace {
 
 constexpr size_t kGeoKeep = 16;   // unreferenced geometries kept for reuse
+
+// The constant-memory request table holds one server's table per device: the
+// first server created on a device takes it, later ones (while it lives) read
+// their table from global memory.
+std::mutex g_const_mu;
+std::map<int, bool> g_const_taken;
+
+bool claim_const_table(int device) {
+    std::lock_guard<std::mutex> lk(g_const_mu);
+    if (g_const_taken[device]) return false;
+    g_const_taken[device] = true;
+    return true;
+}
+
+void release_const_table(int device) {
+    std::lock_guard<std::mutex> lk(g_const_mu);
+    g_const_taken[device] = false;
+}
 
 // Key of a geometry: everything its tables depend on.
 std::string geometry_key(const Request *r) {
@@ -366,7 +385,8 @@ bsgd_status round_graph(bsgd_server *S, int mask, cudaGraphExec_t *out) {
     cudaMemsetAsync(&S->d_ctl->next[0], 0, kRoundClasses * sizeof(unsigned long long), S->round_stream);
     bsgd_status st = launch_round_sample(S->d_table, S->d_ctl, S->prm.max_slots, S->round_stream);
     for (int c = 0; c < kRoundClasses && !st; ++c)
-        if (mask & (1 << c)) st = launch_round_solve(S->d_table, S->d_ctl, c, S->grid[c], S->round_stream);
+        if (mask & (1 << c))
+            st = launch_round_solve(S->d_table, S->d_ctl, c, S->const_table, S->grid[c], S->round_stream);
     if (!st) st = launch_round_update(S->d_table, S->d_ctl, S->prm.max_slots, S->round_stream);
     cudaError_t e = cudaStreamEndCapture(S->round_stream, &graph);
     BSGD_TRY(st);
@@ -407,6 +427,7 @@ bsgd_status upload_table(bsgd_server *S) {
     S->class_mask = mask;
     if (n) BSGD_CUDA(cudaMemcpyAsync(S->d_table, S->h_table, sizeof(ReqDesc) * n,
                                      cudaMemcpyHostToDevice, S->round_stream));
+    if (S->const_table) BSGD_TRY(upload_round_const_table(S->h_table, n, S->round_stream));
     BSGD_CUDA(cudaMemcpyAsync(S->d_ctl, S->h_ctl, sizeof(RoundCtl), cudaMemcpyHostToDevice,
                               S->round_stream));
     BSGD_CUDA(cudaStreamSynchronize(S->round_stream));
@@ -582,11 +603,13 @@ extern "C" bsgd_status bsgd_server_create(const bsgd_server_params *p, bsgd_serv
         BSGD_CUDA(cudaHostAlloc((void **)&S->h_ctl, sizeof(RoundCtl), cudaHostAllocDefault));
         std::memset(S->h_ctl, 0, sizeof(RoundCtl));
         BSGD_CUDA(cudaMemset(S->d_ctl, 0, sizeof(RoundCtl)));
-        for (int c = 0; c < kRoundClasses; ++c) S->grid[c] = round_persistent_grid(c);
+        S->const_table = claim_const_table(p->device);   // max_slots <= 64 = kRoundConstSlots
+        for (int c = 0; c < kRoundClasses; ++c) S->grid[c] = round_persistent_grid(c, S->const_table);
         return BSGD_OK;
     };
     bsgd_status st = init();
     if (st) {
+        if (S->const_table) release_const_table(p->device);
         for (auto &kv : S->graphs) cudaGraphExecDestroy(kv.second);
         cudaFree(S->d_table);
         cudaFree(S->d_ctl);
@@ -634,6 +657,7 @@ extern "C" bsgd_status bsgd_server_destroy(bsgd_server *S) {
     cudaFreeHost(S->h_ctl);
     cudaStreamDestroy(S->round_stream);
     for (cudaStream_t a : S->admit_streams) cudaStreamDestroy(a);
+    if (S->const_table) release_const_table(S->prm.device);
     delete S;
     return BSGD_OK;
 }

@@ -556,17 +556,32 @@ __device__ __forceinline__ int round_entry(const ReqDesc *T, int lo, int hi, lon
     return r;
 }
 
+// The request table of one server per device in constant memory: the
+// persistent passes read a request's geometry and solver arguments through
+// the constant cache, as the plain kernels read their parameters (a lone
+// 256^3 request served: 76 against 99 ms for two epochs with the arguments
+// staged in shared memory). Other servers on the same device use the table in
+// global memory.
+__constant__ ReqDesc c_round_table[kRoundConstSlots];
+
+bsgd_status upload_round_const_table(const ReqDesc *h, int n, cudaStream_t st) {
+    if (n > kRoundConstSlots) return fail(BSGD_ERR_INVALID_ARG, "too many entries for the constant table");
+    if (n > 0)
+        BSGD_CUDA(cudaMemcpyToSymbolAsync(c_round_table, h, sizeof(ReqDesc) * n, 0,
+                                          cudaMemcpyHostToDevice, st));
+    return BSGD_OK;
+}
+
 // Persistent kernel of one class of requests (MULTI: several column blocks
 // per iteration; T: storage type): CTA-sized work items (one detector tile of
 // one view of one pair, or of one drawn row block with several column blocks)
-// handed out by the class's atomic counter. The request's geometry and solver
-// pointers are copied into shared memory when the CTA moves to another request,
-// so that the passes read them from there (as the plain kernels read their
-// parameters) instead of from the table in global memory, where they would
-// compete with the gathers for L1.
-template <bool MULTI, typename T>
-__global__ void __launch_bounds__(128, MULTI ? 7 : 10) round_solve_kernel(const ReqDesc *__restrict__ T_,
-                                                          RoundCtl *__restrict__ C) {
+// handed out by the class's atomic counter. CT: the table is c_round_table;
+// otherwise it is T_ in global memory, and a CTA copies the request's
+// geometry and solver arguments into shared memory when it moves to another
+// request, so that they do not compete with the gathers for L1.
+template <bool MULTI, typename T, bool CT>
+__global__ void __launch_bounds__(128, CT ? 1 : (MULTI ? 7 : 10))
+    round_solve_kernel(const ReqDesc *__restrict__ T_, RoundCtl *__restrict__ C) {
     constexpr int CLS = 3 * (MULTI ? 1 : 0) + (sizeof(T) == 4 ? BSGD_F32
                                                : std::is_same<T, __nv_bfloat16>::value ? BSGD_BF16
                                                                                        : BSGD_F16);
@@ -581,6 +596,23 @@ __global__ void __launch_bounds__(128, MULTI ? 7 : 10) round_solve_kernel(const 
         __syncthreads();   // the previous item is done with sG / sS; s_item is visible
         const long long item = s_item;
         if (item >= C->total_items[CLS] || lo >= hi) return;
+        if (CT) {
+            int e = lo;
+            while (e + 1 < hi && c_round_table[e + 1].work_begin <= item) ++e;
+            const ReqDesc &q = c_round_table[e];
+            __syncthreads();   // every thread has read s_item
+            if (!q.active || item >= q.work_begin + q.work_count) continue;
+            long long local = item - q.work_begin;
+            const int slot = (int)(local % q.G.max_views);
+            local /= q.G.max_views;
+            const int tile = (int)(local % q.max_tiles);
+            const int p = (int)(local / q.max_tiles);
+            const T *x = reinterpret_cast<const T *>(q.x);
+            if (!MULTI) fpbp_solve_body<T>(q.G, q.S, x, tile, slot, p);
+            else if (q.kN <= 2) fpbpm_solve_body<T, 2>(q.G, q.S, x, tile, slot, p);
+            else fpbpm_solve_body<T, 4>(q.G, q.S, x, tile, slot, p);
+            continue;
+        }
         const int e = round_entry(T_, lo, hi, item);
         const ReqDesc &q = T_[e];
         if (e != cur) {
@@ -608,33 +640,36 @@ __global__ void __launch_bounds__(128, MULTI ? 7 : 10) round_solve_kernel(const 
 }
 
 namespace {
-template <bool MULTI, typename T>
-const void *round_kernel_ptr() { return (const void *)round_solve_kernel<MULTI, T>; }
-const void *round_kernel(int cls) {
+template <bool MULTI, typename T, bool CT>
+const void *round_kernel_ptr() { return (const void *)round_solve_kernel<MULTI, T, CT>; }
+template <bool CT>
+const void *round_kernel_of(int cls) {
     switch (cls) {
-    case 0: return round_kernel_ptr<false, float>();
-    case 1: return round_kernel_ptr<false, __nv_bfloat16>();
-    case 2: return round_kernel_ptr<false, __half>();
-    case 3: return round_kernel_ptr<true, float>();
-    case 4: return round_kernel_ptr<true, __nv_bfloat16>();
-    default: return round_kernel_ptr<true, __half>();
+    case 0: return round_kernel_ptr<false, float, CT>();
+    case 1: return round_kernel_ptr<false, __nv_bfloat16, CT>();
+    case 2: return round_kernel_ptr<false, __half, CT>();
+    case 3: return round_kernel_ptr<true, float, CT>();
+    case 4: return round_kernel_ptr<true, __nv_bfloat16, CT>();
+    default: return round_kernel_ptr<true, __half, CT>();
     }
 }
+const void *round_kernel(int cls, bool ct) { return ct ? round_kernel_of<true>(cls) : round_kernel_of<false>(cls); }
 }  // namespace
 
-int round_persistent_grid(int cls) {
+int round_persistent_grid(int cls, bool ct) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int a = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, round_kernel(cls), 128, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, round_kernel(cls, ct), 128, 0);
     cudaGetLastError();
     return sms * std::max(1, a);
 }
 
-bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int cls, int grid, cudaStream_t st) {
+bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int cls, bool ct, int grid,
+                               cudaStream_t st) {
     void *args[] = {(void *)&table, (void *)&ctl};
-    BSGD_CUDA(cudaLaunchKernel(round_kernel(cls), dim3(grid), dim3(128), args, 0, st));
+    BSGD_CUDA(cudaLaunchKernel(round_kernel(cls, ct), dim3(grid), dim3(128), args, 0, st));
     return BSGD_OK;
 }
 

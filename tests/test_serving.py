@@ -212,3 +212,25 @@ def test_several_column_blocks_per_iteration_served():
         rp = B.bsgd_solve(gg, prm, y, x_plain)
         assert rep["updates"] == rp["updates"]
         assert _rel(x_srv, x_plain) <= (2e-3 if prm.storage == B.BF16 else 1e-5)
+
+
+@pytest.mark.gpu
+def test_two_servers_on_one_device():
+    """The first server on a device reads its request table from constant
+    memory, a second one (alive at the same time) from global memory: both
+    give the plain solver's result."""
+    geo = cone(48, 72)
+    y, gg = _data(geo, 8)
+    p = params(seed=9)
+    a = B.Server(budget_bytes=4 << 30, max_slots=4)
+    b = B.Server(budget_bytes=4 << 30, max_slots=4)
+    try:
+        ia, ib = a.submit(geo, 4, 4, p, y), b.submit(geo, 4, 4, p, y)
+        xa, _ = a.wait(ia)
+        xb, _ = b.wait(ib)
+    finally:
+        b.close()
+        a.close()
+    x_plain = np.zeros(gg.n_cols, dtype=np.float32)
+    B.bsgd_solve(gg, p, y, x_plain)
+    assert _rel(xa, x_plain) <= 1e-5 and _rel(xb, x_plain) <= 1e-5
