@@ -329,6 +329,7 @@ struct ReqDesc {
     int64_t work_begin;      // first FP / BP work item of this request in a round
     int64_t work_count;      // max_tiles * max_views * (pairs, or row blocks when kN > 1)
     int64_t max_block_cols;  // voxels of the largest column block
+    int64_t target;          // iterations of the request (no draw past the last)
 };
 
 // The round's work items come in classes, each run by its own persistent
@@ -349,6 +350,7 @@ __host__ __device__ inline int round_class(int kN, int dtype) { return 3 * (kN >
 
 // Fill a request descriptor from a live state (solver.cu).
 bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out);
+bsgd_status state_first_draw(bsgd_state *s, cudaStream_t st);
 // Device bytes state_create allocates for this geometry and these parameters,
 // and the transient set-up buffers on top (solver.cu).
 size_t state_bytes(const bsgd_geometry_desc &d, int M, int N, const bsgd_solve_params &p,
@@ -358,8 +360,6 @@ bsgd_status convert(const void *in, bsgd_dtype it, void *out, bsgd_dtype ot, int
                     cudaStream_t st);
 
 // Round kernels of the server (enqueued once into a captured graph).
-bsgd_status launch_round_sample(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
-                                cudaStream_t st);
 // ct: read the table from the device's constant copy (upload_round_const_table)
 bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int cls, bool ct, int grid,
                                cudaStream_t st);

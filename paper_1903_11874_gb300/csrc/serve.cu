@@ -5,19 +5,21 @@
 //              order while slots and the byte budget allow, builds each one's
 //              geometry and solver state (power-iteration step, unless a
 //              request with the same geometry and step rule ran before: its
-//              step is reused) and hands the ready request to the round thread;
+//              step is reused), draws its first iteration's blocks and hands
+//              the ready request to the round thread;
 //   rounds     keeps a device table of the resident requests and replays one
-//              captured CUDA graph per round: sampler of every request, then
-//              persistent kernels (FP, residual and BP of each ray; one per
-//              class of request present: one or several column blocks per
-//              iteration x storage type) that share all requests' detector
-//              tiles through atomic work counters, then every request's block
-//              update. After the last iteration of a request the round thread
+//              captured CUDA graph per round: persistent kernels (FP,
+//              residual and BP of each ray; one per class of request present:
+//              one or several column blocks per iteration x storage type) that
+//              share all requests' detector tiles through atomic work
+//              counters, then every request's block update with the draw of
+//              its next iteration beside it, then the promotion of those
+//              draws. After the last iteration of a request the round thread
 //              copies its image out, and once that copy has finished it frees
 //              the request and releases its budget.
-// The graph never changes: the kernels read the table and the number of
-// entries from device memory, which the round thread rewrites between rounds
-// when requests join or leave.
+// A graph is kept per set of classes present: the kernels read the table and
+// the number of entries from memory, which the round thread rewrites between
+// rounds when requests join or leave.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -324,9 +326,10 @@ bsgd_status admit_one(bsgd_server *S, Request *r, cudaStream_t stream) {
     if (!r->stage) return fail(BSGD_ERR_OOM, "pinned staging buffer");
     r->upd_host = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(r->stage) + (size_t)C * 4 + 32);
     BSGD_CUDA(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
-    BSGD_CUDA(cudaStreamSynchronize(stream));
     ReqDesc tmp;
     BSGD_TRY(state_descriptor(r->st, r->x, &tmp));   // rejects what rounds cannot run
+    BSGD_TRY(state_first_draw(r->st, stream));        // iteration 0's blocks, before the first round
+    BSGD_CUDA(cudaStreamSynchronize(stream));
     return BSGD_OK;
 }
 
@@ -373,7 +376,8 @@ void admission_loop(bsgd_server *S, cudaStream_t stream) {
 }
 
 // The round graph for a set of request classes (bit c = class c present):
-// sampler, the persistent kernel of each present class, block updates.
+// the persistent kernel of each present class, then the block updates with
+// the next iteration's draws, and the promotion of those draws.
 bsgd_status round_graph(bsgd_server *S, int mask, cudaGraphExec_t *out) {
     auto it = S->graphs.find(mask);
     if (it != S->graphs.end()) {
@@ -383,7 +387,7 @@ bsgd_status round_graph(bsgd_server *S, int mask, cudaGraphExec_t *out) {
     cudaGraph_t graph = nullptr;
     BSGD_CUDA(cudaStreamBeginCapture(S->round_stream, cudaStreamCaptureModeThreadLocal));
     cudaMemsetAsync(&S->d_ctl->next[0], 0, kRoundClasses * sizeof(unsigned long long), S->round_stream);
-    bsgd_status st = launch_round_sample(S->d_table, S->d_ctl, S->prm.max_slots, S->round_stream);
+    bsgd_status st = BSGD_OK;
     for (int c = 0; c < kRoundClasses && !st; ++c)
         if (mask & (1 << c))
             st = launch_round_solve(S->d_table, S->d_ctl, c, S->const_table, S->grid[c], S->round_stream);
@@ -414,6 +418,7 @@ bsgd_status upload_table(bsgd_server *S) {
             ReqDesc d;
             BSGD_TRY(state_descriptor(r->st, r->x, &d));
             if (round_class(d.kN, d.dtype) != cls) continue;
+            d.target = r->target;
             d.work_begin = begin;
             begin += d.work_count;
             S->h_table[n++] = d;

@@ -649,41 +649,53 @@ __global__ void __launch_bounds__(256) update_kernel(const DeviceGeom G, const S
     update_body<T>(G, S, x, xlo, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
-// Serving rounds: the sampler of every resident request (one CTA each) and the
-// block updates of every resident request (grid rows = table entries).
-__global__ void __launch_bounds__(kSampleThreads) round_sample_kernel(const ReqDesc *__restrict__ T,
-                                                                       const RoundCtl *__restrict__ C) {
-    const int r = blockIdx.x;
-    if (r >= C->n || !T[r].active) return;
-    sample_body(T[r].A);
-}
-
+// Serving rounds. A request's draws alternate between two work lists: the
+// round's passes use list 0; CTA 0 of the request's row of the update launch
+// draws the next iteration into list 1 (its draw needs only the residual
+// table, final once the round's FPs are done), so the draw runs beside the
+// update as in bsgd_block_step; then the promote launch copies list 1 into
+// list 0. The first draw of a request is made at its admission. No draw is
+// made past the request's last iteration.
 __global__ void __launch_bounds__(256) round_update_kernel(const ReqDesc *__restrict__ T,
                                                            const RoundCtl *__restrict__ C) {
     const int r = blockIdx.y;
     if (r >= C->n || !T[r].active) return;
     const ReqDesc &q = T[r];
+    if (blockIdx.x == 0) {
+        if (*q.A.iter < q.target) sample_body(q.A);
+        return;
+    }
     for (int c = 0; c < q.kN; ++c) {   // every drawn column block
         if (q.dtype == BSGD_F32)
-            update_body<float>(q.G, q.S, (float *)q.x, nullptr, c, blockIdx.x, gridDim.x);
+            update_body<float>(q.G, q.S, (float *)q.x, nullptr, c, blockIdx.x - 1, gridDim.x - 1);
         else if (q.dtype == BSGD_BF16)
             update_body<__nv_bfloat16>(q.G, q.S, (__nv_bfloat16 *)q.x, (__nv_bfloat16 *)q.xlo, c,
-                                       blockIdx.x, gridDim.x);
+                                       blockIdx.x - 1, gridDim.x - 1);
         else
-            update_body<__half>(q.G, q.S, (__half *)q.x, (__half *)q.xlo, c, blockIdx.x, gridDim.x);
+            update_body<__half>(q.G, q.S, (__half *)q.x, (__half *)q.xlo, c, blockIdx.x - 1,
+                                gridDim.x - 1);
     }
 }
 
-bsgd_status launch_round_sample(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
-                                cudaStream_t st) {
-    round_sample_kernel<<<max_slots, kSampleThreads, 0, st>>>(table, ctl);
-    BSGD_CUDA(cudaGetLastError());
-    return BSGD_OK;
+// List 1 (the next iteration's draw) into list 0, one CTA per request.
+__global__ void __launch_bounds__(256) round_promote_kernel(const ReqDesc *__restrict__ T,
+                                                            const RoundCtl *__restrict__ C) {
+    const int r = blockIdx.x;
+    if (r >= C->n || !T[r].active) return;
+    const ReqDesc &q = T[r];
+    const int *src = reinterpret_cast<const int *>(q.A.work);
+    int *dst = reinterpret_cast<int *>(const_cast<Work *>(q.S.work));
+    static_assert(sizeof(Work) % 4 == 0, "word copy");
+    for (int k = threadIdx.x; k < (int)(sizeof(Work) / 4); k += blockDim.x) dst[k] = src[k];
+    const int nc = kMaxPairs * q.G.max_views;
+    int *cdst = const_cast<int *>(q.S.cells);
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) cdst[k] = q.A.cells[k];
 }
 
 bsgd_status launch_round_update(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
                                 cudaStream_t st) {
-    round_update_kernel<<<dim3(152 * 2, max_slots), 256, 0, st>>>(table, ctl);
+    round_update_kernel<<<dim3(152 * 2 + 1, max_slots), 256, 0, st>>>(table, ctl);
+    round_promote_kernel<<<max_slots, 256, 0, st>>>(table, ctl);
     BSGD_CUDA(cudaGetLastError());
     return BSGD_OK;
 }
@@ -1500,6 +1512,15 @@ static void fill_sample_args(const bsgd_state *s, SampleArgs &A, int64_t k) {
 
 namespace bsgd {
 
+// A served request's first draw (iteration 0, into list 0), on stream st.
+bsgd_status state_first_draw(bsgd_state *s, cudaStream_t st) {
+    SampleArgs A;
+    fill_sample_args(s, A, 0);
+    sample_kernel<<<1, kSampleThreads, 0, st>>>(A);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
 bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out) {
     if (!s || !x || !out) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
     if (!s->fused && (s->kN > kMaxFusedCols || s->p.pair_sampling != BSGD_PAIRS_UNIFORM))
@@ -1509,9 +1530,9 @@ bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out) {
     ReqDesc d{};
     d.G = g->dg;
     d.S = s->dev;
-    d.S.work = work_buf(s, 0);   // served rounds draw, solve and update in one buffer
+    d.S.work = work_buf(s, 0);   // served rounds solve and update with list 0
     d.S.cells = cells_buf(s, 0);
-    fill_sample_args(s, d.A, 0);
+    fill_sample_args(s, d.A, 1);  // the next iteration's draw goes to list 1
     d.A.it = -1;                 // served rounds count iterations on the device
     d.x = x;
     d.xlo = s->xlo;
