@@ -181,7 +181,8 @@ def test_bounded_wait_times_out_and_request_finishes():
 def test_several_column_blocks_per_iteration_served():
     """Requests drawing 2 or 4 column blocks per iteration (the paper's Sec. 5
     and Sec. 6 settings, here with and without detector cells) served among a
-    one-block request: each equals the plain solver's result. More than 4
+    one-block request: each equals the plain solver's result and, replayed
+    from its own draws, the FP64 oracle's (1e-5 FP32, 1e-2 BF16). More than 4
     blocks, or residual pairs with several blocks, are rejected at submit."""
     geo = cone(64, 96)
     y, gg = _data(geo, 9)
@@ -196,6 +197,7 @@ def test_several_column_blocks_per_iteration_served():
         ids = [srv.submit(geo, 4, 4, p2, y), srv.submit(cone(48, 72), 4, 4, params(seed=13), y1),
                srv.submit(geo, 4, 4, p4, y)]
         outs = [srv.wait(i) for i in ids]
+        traces = [srv.read_trace(ids[0]), srv.read_trace(ids[2])]
         with pytest.raises(B.BSGDError) as ei:
             srv.submit(geo, 4, 8, B.SolveParams(alpha=1 / 4, gamma=5 / 8, pair_sampling=B.PAIRS_UNIFORM), y)
         assert ei.value.status == 1
@@ -212,6 +214,32 @@ def test_several_column_blocks_per_iteration_served():
         rp = B.bsgd_solve(gg, prm, y, x_plain)
         assert rep["updates"] == rp["updates"]
         assert _rel(x_srv, x_plain) <= (2e-3 if prm.storage == B.BF16 else 1e-5)
+    # and against the FP64 oracle on the served requests' own draws and step:
+    # two column blocks per iteration (FP32), and all four blocks with one
+    # geometric detector quadrant per view and pair (BF16 storage)
+    from oracle import bsgd as OB
+    from oracle import projector as OP
+    og = OP.Geometry(**geo)
+    mv = gg.info.max_views_per_block
+    for (x_srv, rep), prm, tr, kw, tol in (
+            (outs[0], p2, traces[0], {}, 1e-5),
+            (outs[2], p4, traces[1], dict(cells="geometric", n_cells=4), 1e-2)):
+        sels = []
+        for t in tr:
+            n_p = int(t[0])
+            pairs = [(int(t[1 + 2 * q]), int(t[2 + 2 * q])) for q in range(n_p)]
+            cells = []
+            for q, (i, _) in enumerate(pairs):
+                nv = OP.row_block_views(og, 4, i).size
+                c = np.array(t[1 + 2 * n_p + q * mv:1 + 2 * n_p + q * mv + nv], dtype=np.int64)
+                cells.append(c if kw else None)
+            sels.append(OB.Selection(pairs, cells))
+        po = OB.Params(4, 4, prm.alpha, prm.gamma, rep["mu"], seed=prm.seed, **kw)
+        ost = OB.bsgd(og, y.astype(np.float64), po, len(sels), replay=sels)
+        assert _rel(x_srv, ost.x) <= tol
+        if not kw:   # uniform pairs: the oracle's own sampler draws the same blocks
+            assert [sorted(sel.pairs) for sel in sels] == \
+                [sorted(OB.sample(og, po, k, None, None, None).pairs) for k in range(len(sels))]
 
 
 @pytest.mark.gpu
