@@ -522,6 +522,29 @@ def test_warm_start_one_call_solve_matches_oracle():
     assert rel_l2(OB.bsgd(og, y, OB.Params(M, N, 0.25, 0.25, mu, seed=3), 48).x, ost.x) > 1e-3
 
 
+@pytest.mark.parametrize("extra", [dict(auto_mu=True), dict(tv_lambda=0.02, tv_iters=10)])
+def test_warm_start_with_auto_mu_or_tv_matches_oracle(extra):
+    """The start from x0 combined with Algorithm 3 (whose first residual norm
+    is the warm start's) and with Algorithm 4 (the prox after every epoch):
+    config 1, four epochs of uniform draws, against the oracle from the same
+    x0; Algorithm 3's step decisions agree."""
+    s, og, gg, y, mu, xt = problem("config1")
+    M, N = s["M"], s["N"]
+    x0 = warm_x0(og, xt, 34)
+    mu0 = 2.0 * mu if extra.get("auto_mu") else mu
+    prm = B.SolveParams(alpha=0.25, gamma=0.25, epochs=4, step_rule=B.STEP_FIXED, mu=mu0, seed=5,
+                        auto_window=1 if extra.get("auto_mu") else 0, **extra)
+    xh = x0.copy()
+    rep = B.bsgd_solve(gg, prm, y.astype(np.float32), xh)
+    okw = dict(extra)
+    if extra.get("auto_mu"):
+        okw["auto_window"] = 1
+    ost = OB.bsgd(og, y, OB.Params(M, N, 0.25, 0.25, mu0, seed=5, **okw), 64,
+                  x0=x0.astype(np.float64))
+    assert rel_l2(xh, ost.x) <= 1e-5
+    assert rep["mu"] == pytest.approx(ost.mu, rel=1e-9)
+
+
 @pytest.mark.parametrize("storage", [torch.float32, torch.bfloat16])
 def test_warm_start_block_steps_match_oracle(storage):
     """cone_small, residual-weighted pairs with geometric cells: a state whose
