@@ -118,7 +118,8 @@ def parse():
     return ap.parse_args()
 
 
-LEGS = ("update", "power", "geometry", "bf16", "automu", "tv", "autograd", "precision", "full_solve")
+LEGS = ("update", "power", "geometry", "bf16", "automu", "tv", "autograd", "precision", "full_solve",
+        "shard")
 
 
 def bench_config(world):
@@ -525,6 +526,48 @@ def extra_legs(B, torch, dev, gg, y, mu, prof, iters, updates, peaks, want=lambd
         out.update(tv_leg(B, torch, dev, gg, y, mu, hbm))
     if want("autograd"):
         out.update(autograd_leg(B, torch, dev))
+    if want("shard"):
+        out["NEXT4_shard_one_process"] = shard_leg(B, torch, dev)
+    return out
+
+
+def shard_leg(B, torch, dev, warm=2, iters=20):
+    """The owner-computes path (bsgd_shard_begin / _end) run by one process
+    owning every column block, against the same iterations through
+    bsgd_block_step, on Sec. 5's case-1 set-up (two column blocks per
+    iteration: the setting the paper shards over two GPUs). With one process
+    the exchange is the identity; on N GPUs it is one all-reduce of the buffer
+    per iteration. Per-iteration times, CUDA events."""
+    from paper_1903_11874_gb300 import shard, synth
+    n, nd = PAPER_CASES["case1"]
+    gg = B.Geometry(M=5, N=8, view_block=paper_partition(), **paper_geom(n, nd))
+    vol = torch.from_numpy(synth.ellipsoid_phantom(n, n, n, 10, seed=0).reshape(-1) * KAPPA).to(dev)
+    y = torch.zeros(gg.n_rows, device=dev)
+    B.bsgd_forward_project(gg, vol, y)
+    del vol
+    prm = B.SolveParams(alpha=1 / 5, gamma=2 / 8, step_rule=B.STEP_FIXED, mu=1e-6,
+                        pair_sampling=B.PAIRS_UNIFORM, seed=1)
+    out = {"set_up": "Table 1 case 1: 256^3, 360 views, 400^2 detector, M=5, N=8, "
+                     "alpha=1/5, gamma=2/8 (two column blocks per iteration)"}
+    for name in ("block_step", "sharded"):
+        st = B.State(gg, prm, y)
+        x = torch.zeros(gg.n_cols, device=dev)
+        if name == "sharded":
+            solver = shard.ShardedSolver(st, list(range(gg.N)), lambda b: b,
+                                         torch.empty(0, device=dev))
+            step = solver.block_step
+            out["exchange_floats"] = int(solver.buf.numel())
+        else:
+            step = st.block_step
+        step(x, warm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(x, iters)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name + "_ms_per_iteration"] = round(e0.elapsed_time(e1) / iters, 3)
+        st.close()
     return out
 
 
