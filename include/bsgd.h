@@ -385,15 +385,19 @@ bsgd_status bsgd_state_read_residual(bsgd_state *s, void *out, bsgd_dtype ot, vo
  * Blocks that no process owns are never updated; a block owned by two
  * processes would be counted twice. x: device, the state's storage type,
  * whole-image layout; only the owned blocks' voxels are read or written, and
- * every process's x must be zero at the start (x0 = 0). Supported: uniform
- * pairs, whole views or uniform cells; no TV prox, no automatic step, no
- * replay (INVALID_ARG); call before the first iteration (STATE otherwise).
+ * every process's x must be zero at the start (x0 = 0: the first
+ * bsgd_shard_begin checks it on the device, synchronises `stream` and returns
+ * INVALID_ARG for a non-zero image). Supported: uniform pairs, whole views or
+ * uniform cells; no TV prox, no automatic step, no replay (INVALID_ARG, also
+ * from a later bsgd_state_set_sampling or bsgd_state_set_replay); call before
+ * the first iteration (STATE otherwise).
  * The report's update count is the whole iteration's on every process.
  * bsgd_state_set_shard: owned_blocks host array of n_owned ids; sets
  *   *exchange_len (floats) for the caller's buffer (device, float32, layout
  *   [drawn row block][view of the block][v][u]). Synchronous.
- * bsgd_shard_begin / _end: asynchronous on `stream`; the same `exchange`
- *   buffer must hold the all-reduced sum when _end is called.
+ * bsgd_shard_begin / _end: asynchronous on `stream` (but for the first
+ *   begin's check of x0); the same `exchange` buffer must hold the
+ *   all-reduced sum when _end is called.
  */
 bsgd_status bsgd_state_set_shard(bsgd_state *s, const int32_t *owned_blocks, int n_owned,
                                  int64_t *exchange_len);

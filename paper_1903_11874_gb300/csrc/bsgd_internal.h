@@ -277,6 +277,9 @@ bsgd_status launch_bp_solve(const bsgd_geometry *g, const SolveDev &S, bsgd_dtyp
 // Algorithm 1 from a starting image x (device, storage type): z^j = A^j x_J in
 // every block's band rows and r = y - sum_j z^j; skipped on the device when x
 // is zero (flag: one device int of scratch).
+// flag = 1 if any voxel of x is non-zero (flag cleared first), on stream st.
+bsgd_status launch_nonzero(const bsgd_geometry *g, const void *x, bsgd_dtype st_t, int *flag,
+                           cudaStream_t st);
 bsgd_status launch_warm_start(const bsgd_geometry *g, const SolveDev &S, const void *x,
                               bsgd_dtype st_t, int *flag, cudaStream_t st);
 constexpr int kMaxFusedCols = 4;

@@ -894,6 +894,18 @@ bsgd_status launch_fpbpm_solve(const bsgd_geometry *g, const SolveDev &S, const 
     return BSGD_OK;
 }
 
+bsgd_status launch_nonzero(const bsgd_geometry *g, const void *x, bsgd_dtype st_t, int *flag,
+                           cudaStream_t st) {
+    const int64_t C = g->n_cols();
+    BSGD_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    const int gn = (int)std::max<int64_t>(1, std::min<int64_t>((C + 255) / 256, 152 * 8));
+    if (st_t == BSGD_F32) nonzero_kernel<float><<<gn, 256, 0, st>>>((const float *)x, C, flag);
+    else if (st_t == BSGD_BF16) nonzero_kernel<__nv_bfloat16><<<gn, 256, 0, st>>>((const __nv_bfloat16 *)x, C, flag);
+    else nonzero_kernel<__half><<<gn, 256, 0, st>>>((const __half *)x, C, flag);
+    BSGD_CUDA(cudaGetLastError());
+    return BSGD_OK;
+}
+
 bsgd_status launch_warm_start(const bsgd_geometry *g, const SolveDev &S, const void *x,
                               bsgd_dtype st_t, int *flag, cudaStream_t st) {
     const int64_t C = g->n_cols(), R = g->n_rows();

@@ -1819,6 +1819,15 @@ extern "C" bsgd_status bsgd_shard_begin(bsgd_state *s, void *x, float *exchange,
     const bsgd_geometry *g = s->g;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t k = s->iters;
+    if (k == 0 && !s->zero_start) {
+        // the processes' memories start from x = 0 (a warm start would need
+        // the sum of every process's A^j x0 first): refuse any other image
+        int nz = 0;
+        BSGD_TRY(launch_nonzero(g, x, s->st, s->x0_flag, st));
+        BSGD_CUDA(cudaMemcpyAsync(&nz, s->x0_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        BSGD_CUDA(cudaStreamSynchronize(st));
+        if (nz) return fail(BSGD_ERR_INVALID_ARG, "a sharded state starts from x = 0 on every process");
+    }
     if (k == 0) BSGD_TRY(sync_xT(s, x, st));
     s->dev.work = work_buf(s, k);
     s->dev.cells = cells_buf(s, k);
@@ -1878,6 +1887,8 @@ extern "C" bsgd_status bsgd_state_set_sampling(bsgd_state *s, int pair_sampling,
         return fail(BSGD_ERR_INVALID_ARG, "bad pair sampling");
     if (pair_sampling == BSGD_PAIRS_RESIDUAL && (s->P != 1 || g->M * g->N > kMaxResidualPairs))
         return fail(BSGD_ERR_INVALID_ARG, "residual pair sampling draws one pair per iteration");
+    if (s->owned && (pair_sampling != BSGD_PAIRS_UNIFORM || cells == BSGD_CELLS_GEOMETRIC))
+        return fail(BSGD_ERR_INVALID_ARG, "a sharded state draws uniform pairs and cells");
     if (cells < BSGD_CELLS_NONE || cells > BSGD_CELLS_UNIFORM)
         return fail(BSGD_ERR_INVALID_ARG, "bad cell sampling");
     if (cells != BSGD_CELLS_NONE && n_cells != (g->desc.nv > 1 ? 4 : 2))
@@ -2070,6 +2081,7 @@ extern "C" bsgd_status bsgd_state_read_trace(bsgd_state *s, int32_t *host, int64
 
 extern "C" bsgd_status bsgd_state_set_replay(bsgd_state *s, const int32_t *host, int64_t n_iters) {
     if (!s || (!host && n_iters > 0)) return fail(BSGD_ERR_INVALID_ARG, "NULL argument");
+    if (s->owned && n_iters > 0) return fail(BSGD_ERR_INVALID_ARG, "a sharded state replays no trace");
     if (n_iters < 0) return fail(BSGD_ERR_INVALID_ARG, "n_iters < 0");
     const bsgd_geometry *g = s->g;
     for (int64_t t = 0; t < n_iters; ++t) {

@@ -149,3 +149,30 @@ def test_nccl_exchange_on_the_device():
     assert p.exitcode == 0
     _, og, y, mu = setup()
     assert rel_l2(x, oracle_run(og, y, mu, False).x) <= 1e-5
+
+
+def test_sharded_state_refuses_a_warm_start_and_other_draws():
+    """A sharded state starts from x = 0 (its memories would need every
+    process's A^j x0) and draws uniform pairs only: a non-zero image at the
+    first step, and a later switch to residual-weighted pairs or to a replayed
+    trace, are refused with INVALID_ARG."""
+    from paper_1903_11874_gb300 import binding as B
+    from paper_1903_11874_gb300 import shard
+    s, og, y, mu = setup()
+    gg = gpu_geom(s)
+    st = B.State(gg, gpu_params(B, mu, False), torch.from_numpy(y).cuda())
+    solver = shard.ShardedSolver(st, shard.owned_blocks(gg.N, 0, 1), lambda b: b,
+                                 torch.empty(0, device="cuda:0"))
+    x = torch.zeros(gg.n_cols, device="cuda:0")
+    x[gg.n_cols // 2] = 1.0
+    with pytest.raises(B.BSGDError) as e:
+        solver.block_step(x, 1)
+    assert e.value.status == 1
+    with pytest.raises(B.BSGDError):
+        st.set_sampling(B.PAIRS_RESIDUAL)
+    with pytest.raises(B.BSGDError):
+        st.set_replay(np.full((1, st.trace_stride), -1, dtype=np.int32))
+    x.zero_()
+    solver.block_step(x, 2)              # from zero it steps
+    torch.cuda.synchronize()
+    assert st.query()["iteration"] == 2
