@@ -242,11 +242,12 @@ bool pool_try_alloc(void **p, size_t bytes, cudaStream_t st);
 void pool_free(void *p, cudaStream_t st);
 void state_release(bsgd_state *s, cudaStream_t st);
 
-// Workspace of one TV prox (tv.cu): the input image b and the primal u (FP32),
-// the dual p and its extrapolation r (one float4 per voxel).
+// Workspace of one TV prox (tv.cu): the input image b (FP32), the dual p and
+// its extrapolation r in two buffers (read one, write the other; one float4
+// per voxel).
 struct TvWork {
-    float *b = nullptr, *u = nullptr;
-    float4 *p = nullptr, *r = nullptr;
+    float *b = nullptr;
+    float4 *p = nullptr, *r = nullptr, *r2 = nullptr;
 };
 bsgd_status tv_work_alloc(const bsgd_geometry *g, TvWork &w);
 void tv_work_free(TvWork &w);

@@ -5,14 +5,13 @@
 // and Teboulle 2009): projected gradient with momentum on the dual field p,
 // |p(c)| <= 1, t = b - kappa D^T p, step 1 / (kappa L), L = 4 * ndim.
 //
-// Per iteration two stencil passes over the volume, both HBM-bound:
-//   tv_primal_kernel  u = b - kappa D^T r          (reads r at c and c + e_k)
-//   tv_dual_kernel    p = P(r + D u / (kappa L)),  r = p + w (p - p_prev)
-// Threads are laid out 32 x 8 over (x, y) of one z plane, so voxel coordinates
-// come from the launch indices and neighbours along x share cache lines. The
-// dual fields are one float4 per voxel: with a separate array per component
-// the dual pass ran at 6 % of HBM bandwidth (six read-modify-write streams
-// whose accesses fell on the same memory channels), with float4 it streams.
+// One iteration is one HBM-bound stencil pass (tv_fgp_kernel):
+//   u = b - kappa D^T r            (r at c and c + e_k; u is never stored)
+//   p = P(r + D u / (kappa L)),    r = p + w (p - p_prev)
+// and the final image is one pass of tv_primal_kernel with r = p. The dual
+// fields are one float4 per voxel: with a separate array per component the
+// dual pass ran at 6 % of HBM bandwidth (six read-modify-write streams whose
+// accesses fell on the same memory channels), with float4 it streams.
 #include <algorithm>
 #include <cmath>
 
@@ -73,23 +72,128 @@ __global__ void add_lo_kernel(float *__restrict__ b, const T *__restrict__ lo, i
         b[k] += ldv(lo + k);
 }
 
-__global__ void __launch_bounds__(256) tv_dual_kernel(const TvDims D, const float *__restrict__ u,
-                                                      float step, float wgt, float4 *__restrict__ r,
-                                                      float4 *__restrict__ p_prev) {
-    int x, y, z;
-    int64_t k;
-    if (!tv_voxel(D, x, y, z, k)) return;
-    const int64_t sy = D.nx, sz = (int64_t)D.nx * D.ny;
-    const float uc = u[k];
-    const float4 rc = r[k], po = p_prev[k];
-    const float q0 = rc.x + step * (x >= 1 ? uc - u[k - 1] : 0.f);
-    const float q1 = rc.y + step * (y >= 1 ? uc - u[k - sy] : 0.f);
-    const float q2 = D.ndim == 3 ? rc.z + step * (z >= 1 ? uc - u[k - sz] : 0.f) : 0.f;
-    const float nrm = sqrtf(fmaf(q0, q0, fmaf(q1, q1, q2 * q2)));
-    const float sc = 1.0f / fmaxf(1.0f, nrm);
-    const float p0 = q0 * sc, p1 = q1 * sc, p2 = q2 * sc;
-    p_prev[k] = make_float4(p0, p1, p2, 0.f);
-    r[k] = make_float4(fmaf(wgt, p0 - po.x, p0), fmaf(wgt, p1 - po.y, p1), fmaf(wgt, p2 - po.z, p2), 0.f);
+// Asynchronous global -> shared copies (cp.async): `bytes` from src, or zeros
+// when `valid` is false (src must still be a mapped address; nothing is read).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// One FGP iteration in one pass. A CTA of 256 threads owns a 32 x 8 (x, y)
+// column of the volume over the planes [zb, zb + zchunk) and marches up in z.
+// Plane z's stage holds the extrapolated dual r of the column with one voxel
+// of halo on every side in x and y (34 x 10) and b on the 33 x 9 points whose
+// u the plane's backward differences need (the column and its low-x / low-y
+// neighbours); stages are filled by cp.async two planes ahead in a ring of
+// four. Per plane: u = b - kappa D^T r on the 33 x 9 points (r of this plane
+// and of the next), then the dual of the CTA's own 32 x 8 voxels; u of the
+// plane below is kept from the previous step (a CTA first computes u of the
+// plane below its chunk). r is read from r_in and written to r_out: other CTAs
+// still read r_in's halo. u is formed as tv_primal_kernel forms it, the dual
+// step in the same order of operations as before the fusion.
+constexpr int kTvTx = 32, kTvTy = 8;
+constexpr int kTvRx = kTvTx + 2, kTvRy = kTvTy + 2;   // staged r region
+constexpr int kTvUx = kTvTx + 1, kTvUy = kTvTy + 1;   // u points
+constexpr int kTvStages = 4;
+
+struct TvStage {
+    float4 r[kTvRy][kTvRx];
+    float b[kTvUy][kTvUx];
+};
+
+__global__ void __launch_bounds__(256) tv_fgp_kernel(const TvDims D, const float *__restrict__ b,
+                                                     const float4 *__restrict__ r_in, float kappa,
+                                                     float step, float wgt, int zchunk,
+                                                     float4 *__restrict__ r_out,
+                                                     float4 *__restrict__ p_prev) {
+    __shared__ TvStage stg[kTvStages];
+    __shared__ float su[kTvUy][kTvUx];
+    const int x0 = blockIdx.x * kTvTx, y0 = blockIdx.y * kTvTy;
+    const int zb = blockIdx.z * zchunk, ze = min(D.nz, zb + zchunk);
+    if (zb >= ze) return;
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const bool three = D.ndim == 3;
+    const int zs = three ? max(zb - 1, 0) : zb;
+    // the last plane any step reads: the chunk's top plane's upper neighbour
+    const int zlast = three ? min(ze, D.nz - 1) : ze - 1;
+    auto stage_plane = [&](int z) {   // plane z into stage (z - zs) % kTvStages
+        TvStage &S = stg[(z - zs) % kTvStages];
+        for (int q = tid; q < kTvRx * kTvRy; q += 256) {
+            const int lx = q % kTvRx, ly = q / kTvRx;
+            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            const bool ok = gx >= 0 && gx < D.nx && gy >= 0 && gy < D.ny;
+            cp_async16(&S.r[ly][lx], ok ? r_in + ((int64_t)z * D.ny + gy) * D.nx + gx : r_in, ok);
+        }
+        for (int q = tid; q < kTvUx * kTvUy; q += 256) {
+            const int lx = q % kTvUx, ly = q / kTvUx;
+            const int ux = x0 - 1 + lx, uy = y0 - 1 + ly;
+            const bool ok = ux >= 0 && ux < D.nx && uy >= 0 && uy < D.ny;
+            cp_async4(&S.b[ly][lx], ok ? b + ((int64_t)z * D.ny + uy) * D.nx + ux : b, ok);
+        }
+    };
+    stage_plane(zs);
+    cp_async_commit();
+    if (zs + 1 <= zlast) stage_plane(zs + 1);
+    cp_async_commit();
+    float u_below = 0.f;
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool mine = gx < D.nx && gy < D.ny;
+    for (int z = zs; z < ze; ++z) {
+        // two planes ahead: its stage last held plane z - 2, read two steps ago
+        if (z + 2 <= zlast) stage_plane(z + 2);
+        cp_async_commit();
+        const int64_t k = ((int64_t)z * D.ny + gy) * D.nx + gx;
+        float4 po = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (z >= zb && mine) po = p_prev[k];
+        cp_async_wait<1>();   // planes z and z + 1 have landed (this thread's copies)
+        __syncthreads();      // ... and every thread's
+        const TvStage &C = stg[(z - zs) % kTvStages];
+        const TvStage &Nx = stg[(z + 1 - zs) % kTvStages];
+        for (int q = tid; q < kTvUx * kTvUy; q += 256) {
+            const int lx = q % kTvUx, ly = q / kTvUx;
+            const int ux = x0 - 1 + lx, uy = y0 - 1 + ly;
+            float val = 0.f;
+            if (ux >= 0 && ux < D.nx && uy >= 0 && uy < D.ny) {
+                const float4 rc = C.r[ly][lx];
+                float dt = 0.f;
+                if (ux >= 1) dt += rc.x;
+                if (ux <= D.nx - 2) dt -= C.r[ly][lx + 1].x;
+                if (uy >= 1) dt += rc.y;
+                if (uy <= D.ny - 2) dt -= C.r[ly + 1][lx].y;
+                if (three) {
+                    if (z >= 1) dt += rc.z;
+                    if (z <= D.nz - 2) dt -= Nx.r[ly][lx].z;
+                }
+                val = C.b[ly][lx] - kappa * dt;
+            }
+            su[ly][lx] = val;
+        }
+        __syncthreads();
+        const float uc = su[ty + 1][tx + 1];
+        if (z >= zb && mine) {
+            const float4 rc = C.r[ty + 1][tx + 1];
+            const float q0 = rc.x + step * (gx >= 1 ? uc - su[ty + 1][tx] : 0.f);
+            const float q1 = rc.y + step * (gy >= 1 ? uc - su[ty][tx + 1] : 0.f);
+            const float q2 = three ? rc.z + step * (z >= 1 ? uc - u_below : 0.f) : 0.f;
+            const float nrm = sqrtf(fmaf(q0, q0, fmaf(q1, q1, q2 * q2)));
+            const float sc = 1.0f / fmaxf(1.0f, nrm);
+            const float p0 = q0 * sc, p1 = q1 * sc, p2 = q2 * sc;
+            p_prev[k] = make_float4(p0, p1, p2, 0.f);
+            r_out[k] = make_float4(fmaf(wgt, p0 - po.x, p0), fmaf(wgt, p1 - po.y, p1),
+                                   fmaf(wgt, p2 - po.z, p2), 0.f);
+        }
+        u_below = uc;
+    }
+    cp_async_wait<0>();
 }
 
 bsgd_status convert(const void *in, bsgd_dtype it, void *out, bsgd_dtype ot, int64_t n,
@@ -102,11 +206,11 @@ static TvDims tv_dims(const bsgd_geometry *g) {
 bsgd_status tv_work_alloc(const bsgd_geometry *g, TvWork &w) {
     const TvDims D = tv_dims(g);
     const size_t n = (size_t)D.n;
-    cudaError_t e1 = cudaMalloc(&w.b, n * 4), e2 = cudaMalloc(&w.u, n * 4),
+    cudaError_t e1 = cudaMalloc(&w.b, n * 4), e2 = cudaMalloc(&w.r2, n * 16),
                 e3 = cudaMalloc(&w.p, n * 16), e4 = cudaMalloc(&w.r, n * 16);
     if (e1 || e2 || e3 || e4) {
         cudaGetLastError();
-        cudaFree(w.b), cudaFree(w.u), cudaFree(w.p), cudaFree(w.r);
+        cudaFree(w.b), cudaFree(w.r2), cudaFree(w.p), cudaFree(w.r);
         w = TvWork{};
         return fail(BSGD_ERR_OOM, "TV prox: cannot allocate the dual field");
     }
@@ -115,7 +219,7 @@ bsgd_status tv_work_alloc(const bsgd_geometry *g, TvWork &w) {
 
 void tv_work_free(TvWork &w) {
     cudaFree(w.b);
-    cudaFree(w.u);
+    cudaFree(w.r2);
     cudaFree(w.p);
     cudaFree(w.r);
     w = TvWork{};
@@ -137,11 +241,20 @@ bsgd_status tv_prox_run(const bsgd_geometry *g, void *x, bsgd_dtype xt, double k
     const dim3 grid((D.nx + 31) / 32, (D.ny + 7) / 8, D.nz);
     const float L = 4.0f * D.ndim;
     const float step = (float)(1.0 / (kappa * L));
+    // z-chunks per column: as many as keep every CTA resident in one wave
+    // (7 per SM with the staging ring), at least 8 planes a chunk
+    const int64_t cols = (int64_t)grid.x * grid.y;
+    const int max_chunks = std::max(1, D.nz / 8);
+    const int chunks = (int)std::min<int64_t>(max_chunks, std::max<int64_t>(1, 152 * 7 / cols));
+    const int zchunk = (D.nz + chunks - 1) / chunks;
+    const dim3 fgrid(grid.x, grid.y, (D.nz + zchunk - 1) / zchunk);
+    float4 *rin = w.r, *rout = w.r2;
     double t = 1.0;
     for (int k = 0; k < iters; ++k) {
-        tv_primal_kernel<float><<<grid, 256, 0, st>>>(D, w.b, w.r, (float)kappa, w.u);
         const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
-        tv_dual_kernel<<<grid, 256, 0, st>>>(D, w.u, step, (float)((t - 1.0) / tn), w.r, w.p);
+        tv_fgp_kernel<<<fgrid, 256, 0, st>>>(D, w.b, rin, (float)kappa, step, (float)((t - 1.0) / tn),
+                                             zchunk, rout, w.p);
+        std::swap(rin, rout);
         t = tn;
     }
     if (xt == BSGD_F32)
