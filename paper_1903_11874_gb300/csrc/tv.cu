@@ -93,8 +93,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Plane z's stage holds the extrapolated dual r of the column with one voxel
 // of halo on every side in x and y (34 x 10) and b on the 33 x 9 points whose
 // u the plane's backward differences need (the column and its low-x / low-y
-// neighbours); stages are filled by cp.async two planes ahead in a ring of
-// four. Per plane: u = b - kappa D^T r on the 33 x 9 points (r of this plane
+// neighbours); stages are filled by cp.async kTvAhead planes ahead in a ring
+// of kTvAhead + 2. Per plane: u = b - kappa D^T r on the 33 x 9 points (r of this plane
 // and of the next), then the dual of the CTA's own 32 x 8 voxels; u of the
 // plane below is kept from the previous step (a CTA first computes u of the
 // plane below its chunk). r is read from r_in and written to r_out: other CTAs
@@ -103,7 +103,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 constexpr int kTvTx = 32, kTvTy = 8;
 constexpr int kTvRx = kTvTx + 2, kTvRy = kTvTy + 2;   // staged r region
 constexpr int kTvUx = kTvTx + 1, kTvUy = kTvTy + 1;   // u points
-constexpr int kTvStages = 4;
+constexpr int kTvAhead = 2;                   // planes staged ahead of the one in use
+constexpr int kTvStages = kTvAhead + 2;       // + the plane in use and the one read two steps ago
 
 struct TvStage {
     float4 r[kTvRy][kTvRx];
@@ -140,21 +141,21 @@ __global__ void __launch_bounds__(256) tv_fgp_kernel(const TvDims D, const float
             cp_async4(&S.b[ly][lx], ok ? b + ((int64_t)z * D.ny + uy) * D.nx + ux : b, ok);
         }
     };
-    stage_plane(zs);
-    cp_async_commit();
-    if (zs + 1 <= zlast) stage_plane(zs + 1);
-    cp_async_commit();
+    for (int a = 0; a < kTvAhead; ++a) {
+        if (zs + a <= zlast) stage_plane(zs + a);
+        cp_async_commit();
+    }
     float u_below = 0.f;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool mine = gx < D.nx && gy < D.ny;
     for (int z = zs; z < ze; ++z) {
-        // two planes ahead: its stage last held plane z - 2, read two steps ago
-        if (z + 2 <= zlast) stage_plane(z + 2);
+        // kTvAhead planes ahead: its stage last held plane z - 2, read two steps ago
+        if (z + kTvAhead <= zlast) stage_plane(z + kTvAhead);
         cp_async_commit();
         const int64_t k = ((int64_t)z * D.ny + gy) * D.nx + gx;
         float4 po = make_float4(0.f, 0.f, 0.f, 0.f);
         if (z >= zb && mine) po = p_prev[k];
-        cp_async_wait<1>();   // planes z and z + 1 have landed (this thread's copies)
+        cp_async_wait<kTvAhead - 1>();   // planes z and z + 1 have landed (this thread's copies)
         __syncthreads();      // ... and every thread's
         const TvStage &C = stg[(z - zs) % kTvStages];
         const TvStage &Nx = stg[(z + 1 - zs) % kTvStages];
@@ -242,10 +243,19 @@ bsgd_status tv_prox_run(const bsgd_geometry *g, void *x, bsgd_dtype xt, double k
     const float L = 4.0f * D.ndim;
     const float step = (float)(1.0 / (kappa * L));
     // z-chunks per column: as many as keep every CTA resident in one wave
-    // (7 per SM with the staging ring), at least 8 planes a chunk
+    // (the staging ring's shared memory sets the CTAs per SM), at least 8
+    // planes a chunk
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        BSGD_CUDA(cudaGetDevice(&dev));
+        BSGD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        BSGD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tv_fgp_kernel, 256, 0));
+        resident = std::max(1, sms * per_sm);
+    }
     const int64_t cols = (int64_t)grid.x * grid.y;
     const int max_chunks = std::max(1, D.nz / 8);
-    const int chunks = (int)std::min<int64_t>(max_chunks, std::max<int64_t>(1, 152 * 7 / cols));
+    const int chunks = (int)std::min<int64_t>(max_chunks, std::max<int64_t>(1, resident / cols));
     const int zchunk = (D.nz + chunks - 1) / chunks;
     const dim3 fgrid(grid.x, grid.y, (D.nz + zchunk - 1) / zchunk);
     float4 *rin = w.r, *rout = w.r2;
