@@ -277,6 +277,22 @@ def test_tv_prox_matches_oracle(name):
     assert rel_l2(xg.cpu().double().numpy(), ref) <= 1e-5
 
 
+def test_tv_prox_ragged_volume_matches_oracle():
+    """A 37 x 29 x 19 volume: sides that are no multiple of the fused FGP
+    pass's 32 x 8 columns, and a depth that splits into z-chunks of 10 and 9
+    planes (each chunk recomputes u of the plane below it). The halo, edge and
+    chunk-boundary handling against the oracle's prox."""
+    gg = B.Geometry(M=1, N=1, kind="cone3d", nx=37, ny=29, nz=19, dx=1.0, dy=1.0, dz=1.0, n_views=4,
+                    nu=16, nv=16, du=4.0, dv=4.0, dso=100.0, dsd=200.0)
+    b = np.random.default_rng(5).random(37 * 29 * 19).astype(np.float32)
+    kappa = 0.05
+    xg = torch.from_numpy(b).to(DEV)
+    B.bsgd_tv_prox(gg, xg, kappa, 20)
+    ref = OT.tv_prox(b.astype(np.float64).reshape(19, 29, 37), kappa, 20).reshape(-1)
+    assert rel_l2(xg.cpu().double().numpy(), ref) <= 1e-5
+    gg.close()
+
+
 def test_bsgd_tv_matches_oracle():
     """Algorithm 4: the prox runs after every 1/(alpha gamma) iterations."""
     s, og, gg, y, mu, _ = problem("config1")
