@@ -894,24 +894,31 @@ def serving_leg(B, torch, dev, cfg, seed=3, rate=20.0, budget=160 << 30):
                              seed=100 + k)
 
     # served: submit at the arrival times, continuous batching on the GPU
-    srv = B.Server(budget_bytes=budget, max_slots=16, device=torch.cuda.current_device())
-    t0 = time.perf_counter()
-    ids = []
-    for k, (n, v, st) in enumerate(reqs):
-        delay = t0 + arrivals[k] - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        ids.append(srv.submit(serve_geometry(n, v), M, N, params(st, k), data[(n, v)]))
-    for i in ids:
-        srv.wait(i, timeout_ms=3600 * 1000)
-    makespan = time.perf_counter() - t0
-    stats = srv.stats()
-    srv.close()
-    served = {"p50_ms": round(stats["p50_ms"], 1), "p99_ms": round(stats["p99_ms"], 1),
-              "mean_ms": round(stats["mean_ms"], 1),
-              "value": round(stats["updates"] / makespan / 1e9, 2), "unit": UNIT,
-              "peak_resident": stats["peak_resident"], "peak_gb": round(stats["peak_bytes"] / 1e9, 1),
-              "rounds": stats["rounds"]}
+    def served_stream(priority):
+        srv = B.Server(budget_bytes=budget, max_slots=16, device=torch.cuda.current_device(),
+                       priority=priority)
+        t0 = time.perf_counter()
+        ids = []
+        for k, (n, v, st) in enumerate(reqs):
+            delay = t0 + arrivals[k] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(serve_geometry(n, v), M, N, params(st, k), data[(n, v)]))
+        for i in ids:
+            srv.wait(i, timeout_ms=3600 * 1000)
+        makespan = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.close()
+        return {"p50_ms": round(stats["p50_ms"], 1), "p99_ms": round(stats["p99_ms"], 1),
+                "mean_ms": round(stats["mean_ms"], 1),
+                "value": round(stats["updates"] / makespan / 1e9, 2), "unit": UNIT,
+                "peak_resident": stats["peak_resident"], "peak_gb": round(stats["peak_bytes"] / 1e9, 1),
+                "rounds": stats["rounds"]}
+
+    served = served_stream(B.SERVE_SHARED)
+    # age priority: the oldest resident request advances every round, the
+    # others every second round
+    served_age = served_stream(B.SERVE_AGE)
     # the largest request rate the server sustains on this mix: every request
     # submitted at once (a queue that never runs dry), requests / makespan
     srv = B.Server(budget_bytes=budget, max_slots=16, device=torch.cuda.current_device())
@@ -945,7 +952,7 @@ def serving_leg(B, torch, dev, cfg, seed=3, rate=20.0, budget=160 << 30):
                         "8x8 blocks, %d epochs" % (rate, n_req, list(cfg["sizes"]),
                                                     list(cfg["views"]), cfg["epochs"]),
             "offered_req_per_s": rate,
-            "served": served, "plain_fp32": plain}
+            "served": served, "served_age_priority": served_age, "plain_fp32": plain}
 
 
 # ---------------------------------------------------------------------------

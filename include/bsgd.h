@@ -518,10 +518,22 @@ bsgd_status bsgd_solve(const bsgd_geometry *g, const bsgd_solve_params *p,
  */
 typedef struct bsgd_server bsgd_server;
 
+/*
+ * Round policy. SHARED: every resident request advances one iteration per
+ * round (processor sharing). AGE: the resident request submitted first
+ * advances every round and the others every second round, so the oldest
+ * request gets twice the others' share of the GPU (shorter tail latency for
+ * long requests that share the GPU with later, shorter ones). Results do not
+ * depend on the policy (a request's draws depend only on its own seed and
+ * iteration count).
+ */
+enum { BSGD_SERVE_SHARED = 0, BSGD_SERVE_AGE = 1 };
+
 typedef struct {
     size_t budget_bytes;      /* device memory the resident requests may hold    */
     int max_slots;            /* resident requests at most (<= 64)               */
     int device;               /* CUDA device                                     */
+    int priority;             /* BSGD_SERVE_SHARED or BSGD_SERVE_AGE             */
 } bsgd_server_params;
 
 typedef struct {

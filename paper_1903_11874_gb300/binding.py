@@ -19,6 +19,7 @@ KINDS = {"par2d": PAR2D, "fan2d": FAN2D, "cone3d": CONE3D}
 STEP_STRIP, STEP_BLOCK, STEP_FIXED = 0, 1, 2
 PAIRS_UNIFORM, PAIRS_RESIDUAL = 0, 1
 CELLS_NONE, CELLS_GEOMETRIC, CELLS_UNIFORM = 0, 1, 2
+SERVE_SHARED, SERVE_AGE = 0, 1
 
 # Every symbol include/bsgd.h declares.
 EXPORTS = (
@@ -98,7 +99,8 @@ class Report(ctypes.Structure):
 
 
 class ServerParams(ctypes.Structure):
-    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("device", ctypes.c_int)]
+    _fields_ = [("budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int), ("device", ctypes.c_int),
+                ("priority", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -573,9 +575,10 @@ def bsgd_request_bytes(geo: dict, M: int, N: int, params: SolveParams) -> int:
 class Server:
     """Owning handle of a bsgd_server: submit reconstructions, wait for them."""
 
-    def __init__(self, budget_bytes, max_slots=16, device=0):
+    def __init__(self, budget_bytes, max_slots=16, device=0, priority=None):
         h = ctypes.c_void_p()
-        prm = ServerParams(int(budget_bytes), int(max_slots), int(device))
+        prm = ServerParams(int(budget_bytes), int(max_slots), int(device),
+                           SERVE_SHARED if priority is None else int(priority))
         _check(load().bsgd_server_create(ctypes.byref(prm), ctypes.byref(h)))
         self.handle = h
         self._pending = {}

@@ -329,6 +329,7 @@ struct ReqDesc {
     int dtype;               // storage type
     int max_tiles;           // detector tiles of the largest work box of one view
     int active;
+    int period;              // the request advances in rounds whose index is a multiple of it
     int kN;                  // column blocks per iteration (1: one-block fused pass)
     int64_t work_begin;      // first FP / BP work item of this request in a round
     int64_t work_count;      // max_tiles * max_views * (pairs, or row blocks when kN > 1)
@@ -347,10 +348,16 @@ struct RoundCtl {
     unsigned long long next[kRoundClasses];  // persistent-kernel work counters
     int n;                                   // table entries in use
     int pad;
+    unsigned long long round;                // index of the round (advanced at its end)
     int lo[kRoundClasses], hi[kRoundClasses];
     int64_t total_items[kRoundClasses];      // FP / BP work items of the round, per class
 };
 __host__ __device__ inline int round_class(int kN, int dtype) { return 3 * (kN > 1 ? 1 : 0) + dtype; }
+// Whether a request sits out round `round` (age priority: period 2 for all
+// but the oldest resident request; period 1 advances every round).
+__host__ __device__ inline bool round_skips(int period, unsigned long long round) {
+    return period > 1 && round % (unsigned long long)period != 0;
+}
 
 // Fill a request descriptor from a live state (solver.cu).
 bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out);
@@ -369,7 +376,9 @@ bsgd_status launch_round_solve(const ReqDesc *table, RoundCtl *ctl, int cls, boo
                                cudaStream_t st);
 constexpr int kRoundConstSlots = 64;   // entries of the constant-memory table (one server per device)
 bsgd_status upload_round_const_table(const ReqDesc *h, int n, cudaStream_t st);
-bsgd_status launch_round_update(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
+// the block updates with the next draws, their promotion, and the round's end
+// (the round index advanced)
+bsgd_status launch_round_update(const ReqDesc *table, RoundCtl *ctl, int max_slots,
                                 cudaStream_t st);
 int round_persistent_grid(int cls, bool ct);
 

@@ -57,6 +57,7 @@ struct Request {
     float *x_out = nullptr;       // caller's result buffer
     size_t bytes = 0;             // budget charged while admitted
     int64_t target = 0, done = 0; // iterations
+    int period = 1;               // rounds per iteration while resident (age priority)
     ReqStatus status = kQueued;
     std::string error;
     std::string geo_key;          // geometry cache entry this request holds
@@ -111,6 +112,7 @@ struct bsgd_server {
     RoundCtl *h_ctl = nullptr;    // pinned
     std::map<int, cudaGraphExec_t> graphs;   // round graph per set of classes present
     int class_mask = 0;                      // classes of the current table
+    unsigned long long host_round = 0;       // rounds launched (the device's round index)
     int grid[kRoundClasses] = {};   // persistent grid of each class's kernel
     bool const_table = false;       // this server holds the device's constant request table
     // stats
@@ -408,6 +410,13 @@ bsgd_status round_graph(bsgd_server *S, int mask, cudaGraphExec_t *out) {
 // flight: the round stream is synchronised first).
 bsgd_status upload_table(bsgd_server *S) {
     BSGD_CUDA(cudaStreamSynchronize(S->round_stream));
+    // age priority: the request submitted first advances every round, the
+    // others in every other round (shared: everyone every round)
+    Request *oldest = nullptr;
+    for (Request *r : S->resident)
+        if (!oldest || r->t_submit < oldest->t_submit) oldest = r;
+    for (Request *r : S->resident)
+        r->period = S->prm.priority == BSGD_SERVE_AGE && S->resident.size() > 1 && r != oldest ? 2 : 1;
     // sorted by class (round_class: one or several column blocks per
     // iteration x storage type); work items are numbered within each class
     int n = 0, mask = 0;
@@ -419,6 +428,7 @@ bsgd_status upload_table(bsgd_server *S) {
             BSGD_TRY(state_descriptor(r->st, r->x, &d));
             if (round_class(d.kN, d.dtype) != cls) continue;
             d.target = r->target;
+            d.period = r->period;
             d.work_begin = begin;
             begin += d.work_count;
             S->h_table[n++] = d;
@@ -429,6 +439,7 @@ bsgd_status upload_table(bsgd_server *S) {
         if (S->h_ctl->hi[cls] > S->h_ctl->lo[cls]) mask |= 1 << cls;
     }
     S->h_ctl->n = n;
+    S->h_ctl->round = S->host_round;
     S->class_mask = mask;
     if (n) BSGD_CUDA(cudaMemcpyAsync(S->d_table, S->h_table, sizeof(ReqDesc) * n,
                                      cudaMemcpyHostToDevice, S->round_stream));
@@ -499,9 +510,10 @@ void round_loop(bsgd_server *S) {
             cudaGraphExec_t graph = nullptr;
             if (round_graph(S, S->class_mask, &graph) == BSGD_OK) cudaGraphLaunch(graph, S->round_stream);
             S->rounds++;
+            const unsigned long long t = S->host_round++;
             std::vector<Request *> leaving;
             for (Request *r : S->resident)
-                if (++r->done >= r->target) leaving.push_back(r);
+                if (!round_skips(r->period, t) && ++r->done >= r->target) leaving.push_back(r);
             for (Request *r : leaving) {
                 bsgd_status st = start_finish(S, r);
                 std::lock_guard<std::mutex> lk(S->mu);
@@ -591,6 +603,8 @@ extern "C" bsgd_status bsgd_server_create(const bsgd_server_params *p, bsgd_serv
     *out = nullptr;
     if (p->max_slots < 1 || p->max_slots > 64) return fail(BSGD_ERR_INVALID_ARG, "max_slots in [1, 64]");
     if (p->budget_bytes == 0) return fail(BSGD_ERR_INVALID_ARG, "budget_bytes must be > 0");
+    if (p->priority != BSGD_SERVE_SHARED && p->priority != BSGD_SERVE_AGE)
+        return fail(BSGD_ERR_INVALID_ARG, "priority must be BSGD_SERVE_SHARED or BSGD_SERVE_AGE");
     BSGD_CUDA(cudaSetDevice(p->device));
     bsgd_server *S = new (std::nothrow) bsgd_server();
     if (!S) return fail(BSGD_ERR_OOM, "host allocation failed");

@@ -590,6 +590,7 @@ __global__ void __launch_bounds__(128, CT ? 1 : (MULTI ? 7 : 10))
     __shared__ SolveDev sS;
     static_assert(sizeof(DeviceGeom) % 4 == 0 && sizeof(SolveDev) % 4 == 0, "word copies");
     const int lo = C->lo[CLS], hi = C->hi[CLS];
+    const unsigned long long round = C->round;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(&C->next[CLS], 1ull);
@@ -601,7 +602,7 @@ __global__ void __launch_bounds__(128, CT ? 1 : (MULTI ? 7 : 10))
             while (e + 1 < hi && c_round_table[e + 1].work_begin <= item) ++e;
             const ReqDesc &q = c_round_table[e];
             __syncthreads();   // every thread has read s_item
-            if (!q.active || item >= q.work_begin + q.work_count) continue;
+            if (!q.active || round_skips(q.period, round) || item >= q.work_begin + q.work_count) continue;
             long long local = item - q.work_begin;
             const int slot = (int)(local % q.G.max_views);
             local /= q.G.max_views;
@@ -623,7 +624,7 @@ __global__ void __launch_bounds__(128, CT ? 1 : (MULTI ? 7 : 10))
             for (int k = threadIdx.x; k < (int)(sizeof(SolveDev) / 4); k += blockDim.x) sdst[k] = ssrc[k];
             cur = e;
         }
-        const int active = q.active, max_tiles = q.max_tiles, kN = q.kN;
+        const int active = q.active && !round_skips(q.period, round), max_tiles = q.max_tiles, kN = q.kN;
         const int64_t wb = q.work_begin, wc = q.work_count;
         const T *x = reinterpret_cast<const T *>(q.x);
         __syncthreads();   // sG / sS are complete; every thread has read s_item

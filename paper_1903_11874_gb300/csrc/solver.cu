@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(256) update_kernel(const DeviceGeom G, const S
 __global__ void __launch_bounds__(256) round_update_kernel(const ReqDesc *__restrict__ T,
                                                            const RoundCtl *__restrict__ C) {
     const int r = blockIdx.y;
-    if (r >= C->n || !T[r].active) return;
+    if (r >= C->n || !T[r].active || round_skips(T[r].period, C->round)) return;
     const ReqDesc &q = T[r];
     if (blockIdx.x == 0) {
         if (*q.A.iter < q.target) sample_body(q.A);
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(256) round_update_kernel(const ReqDesc *__rest
 __global__ void __launch_bounds__(256) round_promote_kernel(const ReqDesc *__restrict__ T,
                                                             const RoundCtl *__restrict__ C) {
     const int r = blockIdx.x;
-    if (r >= C->n || !T[r].active) return;
+    if (r >= C->n || !T[r].active || round_skips(T[r].period, C->round)) return;
     const ReqDesc &q = T[r];
     const int *src = reinterpret_cast<const int *>(q.A.work);
     int *dst = reinterpret_cast<int *>(const_cast<Work *>(q.S.work));
@@ -692,10 +692,14 @@ __global__ void __launch_bounds__(256) round_promote_kernel(const ReqDesc *__res
     for (int k = threadIdx.x; k < nc; k += blockDim.x) cdst[k] = q.A.cells[k];
 }
 
-bsgd_status launch_round_update(const ReqDesc *table, const RoundCtl *ctl, int max_slots,
+// The round's last node: every kernel of the round has read its index.
+__global__ void round_tick_kernel(RoundCtl *C) { C->round += 1ull; }
+
+bsgd_status launch_round_update(const ReqDesc *table, RoundCtl *ctl, int max_slots,
                                 cudaStream_t st) {
     round_update_kernel<<<dim3(152 * 2 + 1, max_slots), 256, 0, st>>>(table, ctl);
     round_promote_kernel<<<max_slots, 256, 0, st>>>(table, ctl);
+    round_tick_kernel<<<1, 1, 0, st>>>(ctl);
     BSGD_CUDA(cudaGetLastError());
     return BSGD_OK;
 }
@@ -1544,6 +1548,7 @@ bsgd_status state_descriptor(const bsgd_state *s, void *x, ReqDesc *out) {
     const int tiles = s->fused ? s->max_tiles : s->max_tiles_all;
     d.max_tiles = std::max(1, tiles);
     d.active = s->max_tiles > 0 ? 1 : 0;
+    d.period = 1;
     d.work_count = s->max_tiles > 0 ? (int64_t)tiles * g->max_views * (s->fused ? s->P : s->kM) : 0;
     int64_t maxJ = 0;
     for (int j = 0; j < g->N; ++j) maxJ = std::max(maxJ, g->block_cols(j));

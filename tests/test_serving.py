@@ -60,6 +60,12 @@ def test_request_bytes_rejects_bad_geometry():
         B.bsgd_request_bytes(dict(cone(64, 90), nx=0), 4, 4, params())
 
 
+def test_server_rejects_an_unknown_round_policy():
+    with pytest.raises(B.BSGDError) as e:
+        B.Server(budget_bytes=1 << 30, max_slots=2, priority=7)
+    assert e.value.status == 1
+
+
 # ---- GPU --------------------------------------------------------------------------
 
 def _data(geo, seed):
@@ -262,3 +268,37 @@ def test_two_servers_on_one_device():
     x_plain = np.zeros(gg.n_cols, dtype=np.float32)
     B.bsgd_solve(gg, p, y, x_plain)
     assert _rel(xa, x_plain) <= 1e-5 and _rel(xb, x_plain) <= 1e-5
+
+
+@pytest.mark.gpu
+def test_age_priority_favours_the_oldest_request():
+    """Round policy AGE: while two requests are resident the one submitted
+    first advances every round and the other every second round. A long
+    request L is submitted, then a shorter S of the same set-up: S's latency
+    grows (it advances in every second round only), L is not slowed (it
+    advances every round, as under the shared policy, in rounds that carry
+    less work), and S's image is the same under both policies."""
+    geo = cone(64, 90)
+    y, _ = _data(geo, 4)
+    out = {}
+    for pol in (B.SERVE_SHARED, B.SERVE_AGE):
+        srv = B.Server(budget_bytes=8 << 30, max_slots=4, priority=pol)
+        try:
+            # the first request warms the geometry and step caches, so that
+            # S is admitted within a few rounds of L
+            srv.wait(srv.submit(geo, 4, 4, params(seed=1, epochs=1), y))
+            t0 = time.perf_counter()
+            il = srv.submit(geo, 4, 4, params(seed=2, epochs=120), y)
+            t1 = time.perf_counter()
+            is_ = srv.submit(geo, 4, 4, params(seed=3, epochs=60), y)
+            xs, _ = srv.wait(is_)
+            ts = time.perf_counter() - t1
+            srv.wait(il)
+            tl = time.perf_counter() - t0
+        finally:
+            srv.close()
+        out[pol] = (ts, tl, xs)
+    (ts_sh, tl_sh, xs_sh), (ts_age, tl_age, xs_age) = out[B.SERVE_SHARED], out[B.SERVE_AGE]
+    assert ts_age > 1.2 * ts_sh, (ts_age, ts_sh)
+    assert tl_age <= 1.1 * tl_sh, (tl_age, tl_sh)
+    assert _rel(xs_age, xs_sh) <= 1e-5
